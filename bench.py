@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Throughput of the FETD-PIC particle step on GB300: particle-steps/s.
+
+One step = Faraday update (+ per-triangle field record), the fused
+gather / push / walk / deposit particle kernel, the Ampere update (C^T H b - i
+and the SPAI SpMV) and, every 16 steps, the counting sort by triangle.
+
+Workload (default): magnetized electron-positron pair plasma on a 200,978-
+triangle jittered Delaunay mesh with PEC walls, 20 particles per species per
+triangle (8.04 M), 2-D Maxwell-Juttner momenta kT/mc^2 = 0.1, omega_c/omega_p
+= 0.5, Vay pusher.  The headline runs the FP32 path (cell-local barycentric
+positions); the plain FP64 path runs the same workload beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun, one rank per GPU) every rank advances its own replica
+(weak scaling, no collective on the data path); the time is the max over
+ranks and the value counts all ranks' particle-steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (gather+push+walk+deposit), FP32/batched vs FP64 plain"
+UNIT = "particle-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=317, help="jittered grid side (about 2 side^2 triangles)")
+    ap.add_argument("--ppc", type=int, default=20, help="particles per species per triangle")
+    ap.add_argument("--pusher", default="vay")
+    ap.add_argument("--sort-interval", type=int, default=16)
+    ap.add_argument("--fp64-steps", type=int, default=0, help="0 = min(steps, 100)")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="0 = min(steps, 10)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1707_04333_gb300 import inputs
+    return inputs.pair_plasma(args.side, args.ppc, kT=0.1, wc_over_wp=0.5, seed=2, pusher=args.pusher)
+
+
+def describe(w, args, precision):
+    nf = len(w.mesh.triangles)
+    return (f"pair-plasma {nf} triangles, {w.n_particles} particles (e+p, {args.ppc}/species/triangle), "
+            f"{args.pusher}, {precision}, sort every {args.sort_interval}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_id):
+        self.dev = device_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.06)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons, n = [], [], set(), 0
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            n += 1
+            for nm, v in zip(names[1:], f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+def cpu_oracle(w, sample, steps, warmup=0, seed=5, target_s=None):
+    """Time the FP64 oracle (single thread, as it stands) on a seeded sample of the workload's
+    particles: full steps (Faraday, particles, Ampere with the level-2 SPAI) on the full mesh.
+    With target_s, one calibration step sets the step count for about target_s seconds."""
+    from oracle import oracle
+    from paper_1707_04333_gb300 import inputs
+    oracle.build()
+    sim = oracle.OracleSim(w.mesh.nodes, w.mesh.triangles, w.dt, eps0=inputs.EPS0, mu0=inputs.MU0,
+                           c=inputs.C_LIGHT, spai_level=2, b0=w.b0)
+    rng = np.random.default_rng(seed)
+    n = 0
+    per = max(1, sample // len(w.species))
+    for s in w.species:
+        idx = np.sort(rng.choice(len(s.x), min(per, len(s.x)), replace=False))
+        sim.load(s.q, s.m, s.x[idx], s.u[idx], s.hint[idx])
+        n += len(idx)
+    for _ in range(warmup):
+        sim.step(w.pusher)
+    if target_s:
+        t0 = time.perf_counter()
+        sim.step(w.pusher)
+        steps = int(max(2, min(200, target_s / max(time.perf_counter() - t0, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        sim.step(w.pusher)
+    dt = time.perf_counter() - t0
+    return n * steps / dt, n, dt, steps
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    sample = 250_000
+    val, n, dt, _ = cpu_oracle(w, sample, args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": describe(w, args, "fp64 CPU oracle"),
+                                        "sample_particles": n},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{n} of {w.n_particles} particles, full mesh and field update, "
+                                   f"{args.steps} steps"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1707_04333_gb300 import build_lib, fetdpic
+    if rank == 0:
+        build_lib.build()
+    barrier()
+    build_lib.build()
+
+    w = workload(args)
+    stream = torch.cuda.Stream()          # explicit stream: the context's kernels and the timing events
+
+    def timed_run(precision, steps, warmup, stages=True):
+        sim = fetdpic.Simulation(w, precision=precision, spai_level=2, sort_interval=args.sort_interval,
+                                 time_stages=stages, stream=stream)
+        sim.load()
+        sim.step(warmup, args.pusher).sync()
+        fetdpic.fetdpic_stage_times(sim.h)            # reset the sums
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        fetdpic.fetdpic_step(sim.h, steps, args.pusher)
+        ev1.record(stream)
+        fetdpic.fetdpic_sync(sim.h)
+        torch.cuda.synchronize()
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        st, launches = fetdpic.fetdpic_stage_times(sim.h)
+        pbytes, npart = fetdpic.fetdpic_particle_bytes(sim.h)
+        return sim, ms, st, launches, pbytes, npart
+
+    dev_id = local
+    try:
+        dev_id = str(torch.cuda.get_device_properties(local).uuid)
+        if not dev_id.startswith("GPU-"):
+            dev_id = "GPU-" + dev_id
+    except Exception:
+        pass
+    clocks = ClockSampler(dev_id)
+
+    # ---- headline: FP32 path
+    clocks.start()
+    sim, ms, st, launches, pbytes, npart = timed_run("fp32", args.steps, args.warmup)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    K = args.steps
+    value = npart * K * world / (ms / 1e3)
+    part_ms = st[1] / max(st[3], 1)
+    peak, peak_kind = peaks()
+    achieved = pbytes / (part_ms / 1e3) / 1e9 if part_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "k_particles32 (gather+push+walk+deposit)", "peak_kind": peak_kind,
+                "bytes_per_launch": pbytes}
+    stages = {"faraday_ms": st[0] / max(st[3], 1), "particles_ms": part_ms,
+              "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1)}
+
+    # ---- end to end through the C ABI with page-locked host buffers
+    e2e = None
+    if not args.no_e2e:
+        ke = args.e2e_steps or min(args.steps, 10)
+        hx, hu, hc = [], [], []
+        for k, (inst, sid, n) in enumerate(sim.species):
+            g = sim.read_species(sid)
+            hx.append(torch.from_numpy(g["x"]).pin_memory().numpy())
+            hu.append(torch.from_numpy(g["u"]).pin_memory().numpy())
+            hc.append(torch.from_numpy(g["cell"]).pin_memory().numpy())
+        ox = [torch.empty(a.shape, dtype=torch.float64).pin_memory().numpy() for a in hx]
+        ou = [torch.empty(a.shape, dtype=torch.float64).pin_memory().numpy() for a in hu]
+        oc = [torch.empty(a.shape, dtype=torch.int32).pin_memory().numpy() for a in hc]
+        L = fetdpic.lib()
+        P = fetdpic._ptr
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            for k, (inst, sid, n) in enumerate(sim.species):
+                rc = L.fetdpic_write_particles(sim.h, sid, P(hx[k]), P(hu[k]), P(hc[k]))
+                assert rc == 0, rc
+            fetdpic.fetdpic_step(sim.h, 1, args.pusher)
+            for k, (inst, sid, n) in enumerate(sim.species):
+                rc = L.fetdpic_read(sim.h, inst, None, None, None, sid, P(ox[k]), P(ou[k]), P(oc[k]))
+                assert rc == 0, rc
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        e2e = {"value": npart * ke * world / te, "unit": UNIT, "h2d_bytes_per_step": int(npart * 36),
+               "d2h_bytes_per_step": int(npart * 36), "steps": ke}
+    sim.close()
+    del sim
+
+    # ---- plain FP64 path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        k64 = args.fp64_steps or min(args.steps, 100)
+        sim64, ms64, st64, l64, pb64, np64 = timed_run("fp64", k64, min(args.warmup, 3))
+        if world > 1:
+            t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms64 = float(t.item())
+        v64 = np64 * k64 * world / (ms64 / 1e3)
+        p64 = st64[1] / max(st64[3], 1)
+        fp64 = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64, "particles_ms": p64,
+                "particle_kernel_gbs": pb64 / (p64 / 1e3) / 1e9 if p64 > 0 else None,
+                "speedup_fp32_over_fp64": value / v64}
+        sim64.close()
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, n, dt, ns = cpu_oracle(w, args.cpu_sample, 0, target_s=15.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} of {w.n_particles} particles (seeded), full {len(w.mesh.triangles)}-triangle mesh "
+                         f"and field update, {ns} steps, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": describe(w, args, "fp32 cell-local barycentric"),
+                       "triangles": len(w.mesh.triangles), "particles_per_gpu": npart,
+                       "l2": "inputs larger than L2 (particle state 2 x 161 MB per step)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline,
+            "stages_ms_per_step": stages,
+            "fp64_plain": fp64,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,221 @@
+/*
+ * fetdpic.h - C ABI of the GB300 (sm_103a) charge-conserving relativistic
+ * FETD-PIC particle step on 2-D unstructured triangle meshes.
+ *
+ * Method: Na, Moon, Omelchenko, Teixeira, arXiv:1707.04333.  One time step
+ * n -> n+1 of one or many independent instances ("batched" mode) runs, in
+ * this order, entirely in CUDA kernels on one GPU:
+ *
+ *   1. Faraday update   b^{n+1/2} = b^{n-1/2} - dt C e^n            Sec. II.A, Eq. (semi.dis.curl.1)
+ *   2. gather           E^n from edge DoFs with Whitney 1-forms,
+ *                       B^n = (B^{n+1/2} + B^{n-1/2})/2 from face DoFs
+ *                       with Whitney 2-forms                          Sec. II.B, Sec. II.C(a)
+ *   3. push             relativistic Boris (with/without tan
+ *                       correction), Vay or Higuera-Cary              Sec. II.C, Eqs. (Boris.u1-u4)
+ *   4. move + walk      r^{n+1} = r^n + dt u^{n+1/2}/gamma^{n+1/2},
+ *                       split into the triangles the segment crosses  Eq. (eq.motion.dis)
+ *   5. deposit          i_ab += (Q/dt)(l_a^s l_b^f - l_a^f l_b^s)
+ *                       per crossed triangle                          Sec. II.D, Eq. (I.assign)
+ *   6. Ampere update    e^{n+1} = e^n + dt M (C^T [*mu^-1] b^{n+1/2} - i^{n+1/2}),
+ *                       M = sparse approximate inverse of [*eps]      Sec. II.A, Eq. (semi.dis.curl.2)
+ *
+ * Conventions (all calls):
+ *   - Units are MKS (Sec. I).  2-D TE: E in the plane on edges, B_z on faces,
+ *     particle momentum u = gamma v in the plane (m/s).
+ *   - Every pointer argument is a HOST pointer unless its comment says
+ *     "device".  Inputs are copied during the call; the caller keeps
+ *     ownership of every buffer it passes.  Output buffers are allocated by
+ *     the caller with the sizes stated.
+ *   - Every call returns FETDPIC_OK (0) or a negative fetdpic_status.  On
+ *     error, fetdpic_last_error() returns a one-line description.  Device
+ *     faults found by the kernels (walk limit, non-finite momentum) are
+ *     latched in a device status word and returned by the next
+ *     fetdpic_sync / fetdpic_read / fetdpic_check.
+ *   - A context is bound to the CUDA device current at fetdpic_create and to
+ *     one CUDA stream; calls on one context are not thread-safe.
+ *   - Edges: unless given by the caller, the edges of an instance are all
+ *     node pairs (i, j), i < j, of its triangles, oriented i -> j, numbered in
+ *     lexicographic order of (i, j).  Triangles are re-ordered
+ *     counter-clockwise (nodes 1 and 2 swapped when clockwise); local edge m
+ *     is opposite local node m and runs local node m+1 -> m+2 (mod 3).
+ *   - Boundary edges (one triangle) are PEC walls: e is held at 0 there and
+ *     particles reflect specularly.  The paper does not say how particles
+ *     meet a wall; reflection keeps the path continuous, so charge is still
+ *     conserved exactly.
+ */
+#ifndef FETDPIC_H
+#define FETDPIC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fetdpic_ctx fetdpic_ctx;
+
+typedef enum {
+    FETDPIC_OK = 0,
+    FETDPIC_EINVAL = -1,     /* bad argument (null pointer, size, index, unknown enum) */
+    FETDPIC_ENOMEM = -2,     /* device or host allocation failed */
+    FETDPIC_ECUDA = -3,      /* a CUDA runtime call failed (text in fetdpic_last_error) */
+    FETDPIC_EMESH = -4,      /* degenerate triangle, non-manifold edge, edge list mismatch */
+    FETDPIC_EWALK = -5,      /* a particle crossed more than max_crossings edges in one step */
+    FETDPIC_EOUTSIDE = -6,   /* a loaded particle lies in no triangle */
+    FETDPIC_ENONFINITE = -7, /* a momentum or position became NaN/Inf */
+    FETDPIC_ESTATE = -9      /* call not valid in the current state */
+} fetdpic_status;
+
+typedef enum {
+    FETDPIC_BORIS = 0,       /* Sec. II.C(a), t = beta / gamma_bar            */
+    FETDPIC_BORIS_TAN = 1,   /* Sec. II.C(a), t = beta_hat tan(|beta|/gamma_bar) */
+    FETDPIC_VAY = 2,         /* Sec. II.C(b)                                   */
+    FETDPIC_HC = 3           /* Sec. II.C(c), Higuera-Cary                     */
+} fetdpic_pusher;
+
+typedef enum {
+    /* Plain FP64: global coordinates, same operations in the same order as a
+     * plain FP64 evaluation of the paper's formulas (no FMA contraction), so
+     * one step from the same state gives bit-identical cells, crossed edges,
+     * positions and momenta (Boris-tan excepted: tan is not correctly rounded). */
+    FETDPIC_FP64 = 0,
+    /* FP32 gather/push/deposit with cell-local barycentric positions and
+     * momenta in units of c; FP64 for the Lorentz factor and momentum update
+     * of particles with gamma > 10, for the field update and the checks. */
+    FETDPIC_FP32 = 1
+} fetdpic_precision;
+
+/* Context-wide parameters.  Zero-initialise and set what you need. */
+typedef struct {
+    double eps0, mu0, c;     /* vacuum constants; 0 = CODATA values */
+    int precision;           /* fetdpic_precision */
+    int spai_level;          /* sparsity level k >= 1 of the SPAI of [*eps] (Sec. II.A); 0 = 2;
+                                -1 = exact inverse (dense, only for <= 4096 free edges) */
+    int sort_interval;       /* steps between counting sorts of particles by triangle; 0 = 16, <0 = never */
+    int max_crossings;       /* walk limit per particle per step; 0 = 64 */
+    int check_interval;      /* every k-th step also computes the continuity and Gauss-law
+                                residuals (FP64); 0 = never */
+    int record_walk;         /* > 0: keep up to this many crossed edges per particle of the
+                                last step (debug / parity; costs bandwidth); 0 = off */
+    int block_size;          /* particle-kernel threads per block; 0 = tuned default */
+    int use_graphs;          /* 1 = replay steps from a captured CUDA graph; 0 = plain launches */
+    int time_stages;         /* 1 = record CUDA events between stages (fetdpic_stage_times) */
+    void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
+    /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
+    void *(*dev_alloc)(size_t bytes, void *user);
+    void (*dev_free)(void *ptr, void *user);
+    void *alloc_user;
+} fetdpic_params;
+
+/* One simulation instance (mesh + fields).  Instances share nothing but the
+ * kernel launches (block-diagonal packing). */
+typedef struct {
+    int n_nodes;
+    const double *nodes_xy;  /* [n_nodes][2] node coordinates (m) */
+    int n_tri;
+    const int *triangles;    /* [n_tri][3] node ids in [0, n_nodes) */
+    int n_edges;             /* number of rows in `edges`; ignored when edges == NULL */
+    const int *edges;        /* optional [n_edges][2] edge list (orientation = e and j sign
+                                convention); NULL = derived as described above */
+    const int *edge_tags;    /* optional [n_edges] 0 = free, 1 = PEC (e held at 0);
+                                NULL = PEC exactly on boundary edges */
+    double dt;               /* time step (s) */
+    double b0;               /* initial uniform B_z: b_f = b0 * area_f (face DoF, Eq. (B)) */
+    double e0x, e0y;         /* initial uniform E on free edges: e_k = E0 . (r_j - r_i) (Eq. (E)) */
+    double ext_ex, ext_ey, ext_bz; /* external uniform fields added at each particle */
+} fetdpic_instance;
+
+/* Build the mesh topology, incidence matrices C and S~ (Sec. II.A), Whitney
+ * geometry, [*eps] (Galerkin edge mass matrix), the diagonal [*mu^-1] =
+ * 1/(mu0 A_f), the SPAI M ~ [*eps]^-1 on free edges, and upload everything.
+ * inst[n_inst] are host structs; their arrays are copied.  Returns
+ * FETDPIC_EMESH for degenerate input.  *out is NULL on error. */
+int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *p, int n_inst, const fetdpic_instance *inst);
+
+/* Add one species of n superparticles (charge q, rest mass m) to instance
+ * `inst`.  x: [n][2] positions (m); u: [n][2] momenta u = gamma v (m/s),
+ * taken as u^{n-1/2} (no half-step back-push).  cell_hint: optional [n]
+ * triangle indices to try first (a particle goes to the hint when all its
+ * barycentric coordinates there are >= 0, else to the lowest-index triangle
+ * where they are).  Returns the new species id (>= 0), or FETDPIC_EOUTSIDE if
+ * a point lies in no triangle.  Must precede the first fetdpic_step. */
+int fetdpic_load_particles(fetdpic_ctx *ctx, int inst, double q, double m, long long n,
+                           const double *x, const double *u, const int *cell_hint);
+
+/* Overwrite the state of species `species` (same count as loaded) from host
+ * arrays: x [n][2], u [n][2], cell [n] (instance-local triangle of each point,
+ * e.g. from a previous fetdpic_read; NULL = locate again on the host).  With
+ * `cell` the arrays are copied to the device as they are (fastest from
+ * page-locked memory) and converted there.  Used for checkpoint/restart and
+ * for end-to-end runs that stream the particle state from the host. */
+int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const double *x, const double *u, const int *cell);
+
+/* Overwrite the fields of instance `inst`: e [n_edges] (e^n, PEC entries are
+ * forced to 0) and b [n_tri] (b^{n-1/2}); either may be NULL. */
+int fetdpic_write_fields(fetdpic_ctx *ctx, int inst, const double *e, const double *b);
+
+/* Enqueue nsteps time steps with pusher `pusher` (fetdpic_pusher) on the
+ * context stream.  Asynchronous: returns after the launches. */
+int fetdpic_step(fetdpic_ctx *ctx, long long nsteps, int pusher);
+
+/* Wait for the context stream; return the first latched device status. */
+int fetdpic_sync(fetdpic_ctx *ctx);
+
+/* Copy state of instance `inst` to host buffers (each may be NULL):
+ * e [n_edges] = e^n, b [n_tri] = b^{n-1/2} (the latest face DoFs),
+ * j [n_edges] = i^{n-1/2} of the last step.  Then species `species` (ignored
+ * if x, u and cell are all NULL): x [n][2], u [n][2], cell [n], in load
+ * order.  FP32 mode converts barycentric positions to x = sum_k l_k r_k. */
+int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
+                 int species, double *x, double *u, int *cell);
+
+/* Crossed-edge record of the last step for species `species` (needs
+ * record_walk > 0): cnt [n] crossings per particle; rec [n][record_walk]
+ * the crossed edges (instance-local ids) in crossing order, a wall
+ * reflection stored as -(edge+1).  Load order. */
+int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *rec);
+
+/* Residuals of the latest check step (check_interval > 0), FP64:
+ * dce_max = max over nodes of |q^{n+1}-q^n + dt (S~ i^{n+1/2})_k| / (sum of
+ * |contributions| at k), the discrete continuity equation (Eq. full.dis.cont);
+ * dgl_max = max over nodes of |(S~ d^n - q^n) - (S~ d^0 - q^0)|_k / scale_k,
+ * the discrete Gauss law (Eq. semi.dis.div.2) written with the dual flux
+ * d^n = d^0 + dt sum (C^T [*mu^-1] b - i) that [*eps] e^n approximates
+ * through the SPAI; energy = e.[*eps].e/2 + b.[*mu^-1].b/2 (J per m).
+ * Any output may be NULL. */
+int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double *dgl_max, double *energy);
+
+/* Sizes of instance `inst`: out[0..5] = n_nodes, n_edges, n_tri, n_free_edges,
+ * spai nnz, total particles of the instance. */
+int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6]);
+
+/* The edge list of instance `inst` as used for e and j: edges [n_edges][2]. */
+int fetdpic_read_edges(fetdpic_ctx *ctx, int inst, int *edges);
+
+/* The SPAI of instance `inst` over free edges in CSR with instance-local edge
+ * ids: rowptr [n_free+1] (row = free edge in ascending edge id), col [nnz]
+ * (edge id), val [nnz]; row_edge [n_free].  Any NULL output is skipped. */
+int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_edge, int *col, double *val);
+
+/* Device time per stage, summed over every step enqueued since the previous
+ * call (needs time_stages = 1; CUDA events recorded on the context stream
+ * between stages, read at fetdpic_sync): out[0] Faraday + field record,
+ * out[1] particle kernel, out[2] Ampere (C^T H b - i and the SPAI SpMV),
+ * out[3] steps timed, out[4] sort, out[5] checks, in ms.  *launches = kernels
+ * launched by those steps.  The sums are reset by this call. */
+int fetdpic_stage_times(fetdpic_ctx *ctx, double out[6], long long *launches);
+
+/* Algorithmic bytes of one launch of the particle kernel (particle state read
+ * and written: FP64 2 x 36 B, FP32 2 x 20 B per particle) and the particle
+ * count; the roofline numerator. */
+int fetdpic_particle_bytes(fetdpic_ctx *ctx, double *bytes, long long *n_particles);
+
+const char *fetdpic_last_error(const fetdpic_ctx *ctx);
+
+void fetdpic_destroy(fetdpic_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FETDPIC_H */

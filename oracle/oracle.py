@@ -181,17 +181,23 @@ class OracleSim:
     """
 
     def __init__(self, nodes, triangles, dt, *, eps0, mu0, c, spai_level=2, exact_inverse=False,
-                 b0=0.0, e0=(0.0, 0.0), ext=(0.0, 0.0, 0.0), max_cross=64):
+                 b0=0.0, e0=(0.0, 0.0), ext=(0.0, 0.0, 0.0), max_cross=64, fields=True):
+        """fields=False skips [*eps] and the SPAI (particle-only steps on large meshes)."""
         self.mesh = m = OracleMesh(nodes, triangles)
         self.dt, self.eps0, self.mu0, self.c = dt, eps0, mu0, c
         self.ext = tuple(float(v) for v in ext)
         self.max_cross = max_cross
-        self.star_eps = m.hodge_eps(eps0)
-        Af = self.star_eps[m.free][:, m.free].tocsr()
-        if exact_inverse:
-            Minv = sp.csr_matrix(np.linalg.inv(Af.toarray()))
+        self.has_fields = fields
+        if fields:
+            self.star_eps = m.hodge_eps(eps0)
+            Af = self.star_eps[m.free][:, m.free].tocsr()
+            if exact_inverse:
+                Minv = sp.csr_matrix(np.linalg.inv(Af.toarray()))
+            else:
+                Minv = spai(Af, spai_level)
         else:
-            Minv = spai(Af, spai_level)
+            self.star_eps = sp.csr_matrix((m.ne, m.ne))
+            Minv = sp.csr_matrix((len(m.free), len(m.free)))
         Minv.sort_indices()
         self.Minv = Minv
         self._rp = np.ascontiguousarray(Minv.indptr, np.int64)
@@ -208,12 +214,16 @@ class OracleSim:
         self.species = []
         self.step_count = 0
 
-    def load(self, q, m_, x, u, hint=None):
+    def load(self, q, m_, x, u, hint=None, cell=None):
+        """Add a species; `cell` (if given) is taken as the host triangle of each point as is."""
         x = np.asarray(x, np.float64)
         u = np.asarray(u, np.float64)
-        cell, bad = self.mesh.locate(x[:, 0], x[:, 1], hint)
-        if bad:
-            raise ValueError(f"oracle: {bad} particles outside the mesh")
+        if cell is None:
+            cell, bad = self.mesh.locate(x[:, 0], x[:, 1], hint)
+            if bad:
+                raise ValueError(f"oracle: {bad} particles outside the mesh")
+        else:
+            cell = np.ascontiguousarray(cell, np.int32).copy()
         self.species.append(dict(q=float(q), m=float(m_), x=x[:, 0].copy(), y=x[:, 1].copy(),
                                  ux=u[:, 0].copy(), uy=u[:, 1].copy(), uz=np.zeros(len(x)),
                                  cell=cell))
@@ -251,6 +261,8 @@ class OracleSim:
             status = status or st
             recs.append((cnt, rec))
         if not only_particles:
+            if not self.has_fields:
+                raise ValueError("oracle built with fields=False: particle-only steps")
             r = np.zeros(m.ne)
             lib().ora_curl_h(m.cs, C.c_double(self.mu0), _p(b_new), _p(self.i), _p(r))
             lib().ora_ampere(len(m.free), _p(m.free), _p(self._rp), _p(self._ci), _p(self._v),

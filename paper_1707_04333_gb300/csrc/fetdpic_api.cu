@@ -1,0 +1,848 @@
+// The C ABI of include/fetdpic.h: context, device memory, launch sequence.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "fetdpic_internal.h"
+
+using namespace fetdpic;
+
+namespace {
+
+constexpr double CODATA_EPS0 = 8.8541878128e-12;
+constexpr double CODATA_MU0 = 1.25663706212e-6;
+constexpr double CODATA_C = 299792458.0;
+constexpr long long SPECIES_ALIGN = 1024;   // species storage ranges start on this multiple
+
+struct StagedSpecies {
+    int inst;
+    double q, m;
+    std::vector<int> cell;                   // instance-local
+    std::vector<double> x, y, ux, uy;
+};
+
+}  // namespace
+
+struct fetdpic_ctx {
+    fetdpic_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    std::vector<HostMesh> mesh;
+    std::vector<fetdpic_instance> inst;
+    std::vector<int> cell_off, edge_off, node_off;
+    int F = 0, E = 0, N = 0;
+    long long nfree = 0;
+
+    // device: mesh and fields
+    Geo64 *geo64 = nullptr; Geo32 *geo32 = nullptr; Topo *topo = nullptr;
+    Rec64 *rec64 = nullptr; Rec32 *rec32 = nullptr;
+    double *e = nullptr, *b = nullptr, *d = nullptr, *r = nullptr, *j = nullptr;
+    unsigned long long *ifix = nullptr;
+    int2 *efac = nullptr; double2 *ecoef = nullptr; int *einst = nullptr;
+    double *inst_unit = nullptr, *inst_dt = nullptr;
+    int *edge_off_dev = nullptr;
+    long long *m_rp = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
+    unsigned *status = nullptr;
+    std::vector<double> unit_host;           // per instance (q_ref/dt) 2^-shift
+    std::vector<int> shift;                  // per instance
+
+    // particles
+    std::vector<StagedSpecies> staged;
+    bool finalized = false;
+    std::vector<Species> sp;
+    Species *sp_dev = nullptr;
+    long long P = 0, nblocks = 0;
+    int block = 256;
+    int *cell = nullptr, *cell_tmp = nullptr, *id = nullptr, *id_tmp = nullptr;
+    void *f[4] = {nullptr, nullptr, nullptr, nullptr}, *f_tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+    short *blk_sp = nullptr;
+    int *hist = nullptr, *hoff = nullptr, *scan_tmp = nullptr; long long hist_n = 0;
+    long long *pad_adj = nullptr;
+    int *rec_cnt = nullptr, *rec = nullptr;
+
+    long long steps_done = 0;
+    long long launches_acc = 0;
+    std::vector<cudaEvent_t> ev;             // event pool, grown on demand
+    std::vector<int> ev_stage;               // stage closed by each recorded event (-1 = start of a step)
+    int ev_used = 0;
+    double stage_ms[6] = {0, 0, 0, 0, 0, 0};
+    // reusable device scratch for host <-> device transfers of particle state
+    void *xfer = nullptr; size_t xfer_bytes = 0;
+
+    std::vector<void *> allocs;
+
+    ~fetdpic_ctx()
+    {
+        cudaSetDevice(device);
+        if (stream) cudaStreamSynchronize(stream);
+        for (void *q : allocs) {
+            if (p.dev_free) p.dev_free(q, p.alloc_user);
+            else cudaFree(q);
+        }
+        for (auto &x : ev) cudaEventDestroy(x);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+
+    template <typename T>
+    T *alloc(size_t count)
+    {
+        size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+        void *q = nullptr;
+        if (p.dev_alloc) q = p.dev_alloc(bytes, p.alloc_user);
+        else if (cudaMalloc(&q, bytes) != cudaSuccess) q = nullptr;
+        if (!q) throw std::bad_alloc();
+        allocs.push_back(q);
+        return (T *)q;
+    }
+
+    int fail(int code, const std::string &m)
+    {
+        err = m;
+        return code;
+    }
+
+    int cuda_fail(cudaError_t e, const char *where)
+    {
+        err = std::string(where) + ": " + cudaGetErrorString(e);
+        return FETDPIC_ECUDA;
+    }
+};
+
+#define CK(call)                                                                     \
+    do {                                                                             \
+        cudaError_t _e = (call);                                                     \
+        if (_e != cudaSuccess) return ctx->cuda_fail(_e, #call);                     \
+    } while (0)
+
+template <typename T>
+static int upload(fetdpic_ctx *ctx, T *dst, const T *src, size_t n)
+{
+    if (n == 0) return FETDPIC_OK;
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+    return FETDPIC_OK;
+}
+
+static int map_status(fetdpic_ctx *ctx, unsigned st)
+{
+    if (st & ST_WALK) return ctx->fail(FETDPIC_EWALK, "a particle crossed more than max_crossings edges in one step");
+    if (st & ST_NONFINITE) return ctx->fail(FETDPIC_ENONFINITE, "non-finite momentum or Lorentz factor");
+    if (st) return ctx->fail(FETDPIC_EMESH, "device status " + std::to_string(st));
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int n_inst, const fetdpic_instance *inst)
+{
+    if (!out) return FETDPIC_EINVAL;
+    *out = nullptr;
+    if (!prm || n_inst <= 0 || !inst) return FETDPIC_EINVAL;
+    std::unique_ptr<fetdpic_ctx> holder;
+    try { holder.reset(new fetdpic_ctx()); } catch (...) { return FETDPIC_ENOMEM; }
+    fetdpic_ctx *ctx = holder.get();
+    ctx->p = *prm;
+    auto &P = ctx->p;
+    if (P.eps0 == 0) P.eps0 = CODATA_EPS0;
+    if (P.mu0 == 0) P.mu0 = CODATA_MU0;
+    if (P.c == 0) P.c = CODATA_C;
+    if (P.precision != FETDPIC_FP64 && P.precision != FETDPIC_FP32) return FETDPIC_EINVAL;
+    if (P.sort_interval == 0) P.sort_interval = 16;
+    if (P.max_crossings <= 0) P.max_crossings = 64;
+    if (P.block_size == 0) P.block_size = 256;
+    if (P.block_size < 32 || P.block_size > 256 || (P.block_size & 31) || (SPECIES_ALIGN % P.block_size))
+        return FETDPIC_EINVAL;
+    if (P.record_walk < 0) return FETDPIC_EINVAL;
+    ctx->block = P.block_size;
+    CK(cudaGetDevice(&ctx->device));
+    if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
+    else { CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)); ctx->own_stream = true; }
+
+    // ---- host setup per instance
+    ctx->mesh.resize(n_inst);
+    ctx->inst.assign(inst, inst + n_inst);
+    ctx->cell_off.assign(n_inst + 1, 0);
+    ctx->edge_off.assign(n_inst + 1, 0);
+    ctx->node_off.assign(n_inst + 1, 0);
+    for (int k = 0; k < n_inst; ++k) {
+        const fetdpic_instance &I = inst[k];
+        if (!(I.dt > 0)) return ctx->fail(FETDPIC_EINVAL, "dt must be > 0"), FETDPIC_EINVAL;
+        std::string msg;
+        int rc = build_mesh(ctx->mesh[k], I.n_nodes, I.nodes_xy, I.n_tri, I.triangles,
+                            I.edges ? I.n_edges : 0, I.edges, I.edge_tags, msg);
+        if (rc == FETDPIC_OK) rc = build_hodge(ctx->mesh[k], P.eps0, msg);
+        if (rc == FETDPIC_OK) rc = build_spai(ctx->mesh[k], P.spai_level, msg);
+        if (rc != FETDPIC_OK) {
+            fprintf(stderr, "fetdpic_create: instance %d: %s\n", k, msg.c_str());
+            return rc;
+        }
+        ctx->cell_off[k + 1] = ctx->cell_off[k] + ctx->mesh[k].nf;
+        ctx->edge_off[k + 1] = ctx->edge_off[k] + ctx->mesh[k].ne;
+        ctx->node_off[k + 1] = ctx->node_off[k] + ctx->mesh[k].nn;
+    }
+    ctx->F = ctx->cell_off[n_inst];
+    ctx->E = ctx->edge_off[n_inst];
+    ctx->N = ctx->node_off[n_inst];
+    if ((long long)ctx->F * 4 >= (1LL << 31) || (long long)ctx->E * 2 >= (1LL << 31))
+        return FETDPIC_EINVAL;
+
+    // ---- host images of the device tables
+    std::vector<Geo64> g64(ctx->F);
+    std::vector<Geo32> g32(P.precision == FETDPIC_FP32 ? ctx->F : 0);
+    std::vector<Topo> tp(ctx->F);
+    std::vector<double> e0(ctx->E, 0.0), b0(ctx->F, 0.0), d0(ctx->E, 0.0);
+    std::vector<int2> efac(ctx->E);
+    std::vector<double2> ecoef(ctx->E);
+    std::vector<int> einst(ctx->E);
+    std::vector<long long> mrp(1, 0);
+    std::vector<int> mrow, mci;
+    std::vector<double> mv;
+    std::vector<double> idt(n_inst);
+    for (int k = 0; k < n_inst; ++k) {
+        const HostMesh &M = ctx->mesh[k];
+        const fetdpic_instance &I = inst[k];
+        const int co = ctx->cell_off[k], eo = ctx->edge_off[k], no = ctx->node_off[k];
+        idt[k] = I.dt;
+        for (int f = 0; f < M.nf; ++f) {
+            Geo64 &G = g64[co + f];
+            for (int m = 0; m < 3; ++m) {
+                G.gx[m] = M.gx[3 * f + m]; G.gy[m] = M.gy[3 * f + m];
+                G.X[m] = M.X[3 * f + m]; G.Y[m] = M.Y[3 * f + m];
+            }
+            G.inv2A = M.inv2A[f];
+            G.dt = I.dt;
+            G.hb = 1.0 / (P.mu0 * (0.5 * M.d2A[f]));
+            G.pad = 0;
+            if (!g32.empty()) {
+                Geo32 &H = g32[co + f];
+                for (int m = 0; m < 3; ++m) {
+                    H.G[2 * m] = (float)(P.c * I.dt * M.gx[3 * f + m]);
+                    H.G[2 * m + 1] = (float)(P.c * I.dt * M.gy[3 * f + m]);
+                }
+                H.pad[0] = H.pad[1] = 0.f;
+            }
+            Topo &T = tp[co + f];
+            for (int m = 0; m < 3; ++m) {
+                const int eg = eo + M.tedge[3 * f + m];
+                T.ew[m] = (eg << 1) | (M.tsign[3 * f + m] < 0 ? 1 : 0);
+                T.nb[m] = M.tnb[3 * f + m] < 0 ? -1 : (((co + M.tnb[3 * f + m]) << 2) | M.tnbm[3 * f + m]);
+                T.node[m] = no + M.tri[3 * f + m];
+            }
+            T.inst = k;
+            b0[co + f] = I.b0 * (0.5 * M.d2A[f]);          // b_f = B0 A_f
+        }
+        for (int e = 0; e < M.ne; ++e) {
+            const int a = M.edge[2 * e], bnode = M.edge[2 * e + 1];
+            if (!M.pec[e])
+                e0[eo + e] = I.e0x * (M.xy[2 * bnode] - M.xy[2 * a]) + I.e0y * (M.xy[2 * bnode + 1] - M.xy[2 * a + 1]);
+            efac[eo + e] = make_int2(co + M.efac[2 * e], M.efac[2 * e + 1] < 0 ? -1 : co + M.efac[2 * e + 1]);
+            const double h0 = 1.0 / (P.mu0 * (0.5 * M.d2A[M.efac[2 * e]]));
+            const double h1 = M.efac[2 * e + 1] < 0 ? 0.0 : 1.0 / (P.mu0 * (0.5 * M.d2A[M.efac[2 * e + 1]]));
+            ecoef[eo + e] = make_double2(M.efsign[2 * e] * h0, M.efsign[2 * e + 1] * h1);
+            einst[eo + e] = k;
+        }
+        // d^0 = [*eps] e^0 over all edges
+        for (int e = 0; e < M.ne; ++e) {
+            double s = 0.0;
+            for (long long q = M.h_rp[e]; q < M.h_rp[e + 1]; ++q) s += M.h_v[q] * e0[eo + M.h_ci[q]];
+            d0[eo + e] = s;
+        }
+        for (size_t a = 0; a < M.free_edges.size(); ++a) {
+            mrow.push_back(eo + M.free_edges[a]);
+            for (long long q = M.m_rp[a]; q < M.m_rp[a + 1]; ++q) {
+                mci.push_back(eo + M.m_ci[q]);
+                mv.push_back(I.dt * M.m_v[q]);
+            }
+            mrp.push_back((long long)mci.size());
+        }
+    }
+    ctx->nfree = (long long)mrow.size();
+    try {
+        ctx->geo64 = ctx->alloc<Geo64>(ctx->F);
+        if (P.precision == FETDPIC_FP32) {
+            ctx->geo32 = ctx->alloc<Geo32>(ctx->F);
+            ctx->rec32 = ctx->alloc<Rec32>(ctx->F);
+        } else {
+            ctx->rec64 = ctx->alloc<Rec64>(ctx->F);
+        }
+        ctx->topo = ctx->alloc<Topo>(ctx->F);
+        ctx->e = ctx->alloc<double>(ctx->E);
+        ctx->b = ctx->alloc<double>(ctx->F);
+        ctx->d = ctx->alloc<double>(ctx->E);
+        ctx->r = ctx->alloc<double>(ctx->E);
+        ctx->j = ctx->alloc<double>(ctx->E);
+        ctx->ifix = ctx->alloc<unsigned long long>(ctx->E);
+        ctx->efac = ctx->alloc<int2>(ctx->E);
+        ctx->ecoef = ctx->alloc<double2>(ctx->E);
+        ctx->einst = ctx->alloc<int>(ctx->E);
+        ctx->inst_unit = ctx->alloc<double>(n_inst);
+        ctx->inst_dt = ctx->alloc<double>(n_inst);
+        ctx->edge_off_dev = ctx->alloc<int>(n_inst + 1);
+        ctx->m_rp = ctx->alloc<long long>(mrp.size());
+        ctx->m_row = ctx->alloc<int>(mrow.size());
+        ctx->m_ci = ctx->alloc<int>(mci.size());
+        ctx->m_v = ctx->alloc<double>(mv.size());
+        ctx->status = ctx->alloc<unsigned>(1);
+    } catch (const std::bad_alloc &) {
+        return FETDPIC_ENOMEM;
+    }
+    int rc = FETDPIC_OK;
+    rc = rc ? rc : upload(ctx, ctx->geo64, g64.data(), g64.size());
+    if (!g32.empty()) rc = rc ? rc : upload(ctx, ctx->geo32, g32.data(), g32.size());
+    rc = rc ? rc : upload(ctx, ctx->topo, tp.data(), tp.size());
+    rc = rc ? rc : upload(ctx, ctx->e, e0.data(), e0.size());
+    rc = rc ? rc : upload(ctx, ctx->b, b0.data(), b0.size());
+    rc = rc ? rc : upload(ctx, ctx->d, d0.data(), d0.size());
+    rc = rc ? rc : upload(ctx, ctx->efac, efac.data(), efac.size());
+    rc = rc ? rc : upload(ctx, ctx->ecoef, ecoef.data(), ecoef.size());
+    rc = rc ? rc : upload(ctx, ctx->einst, einst.data(), einst.size());
+    rc = rc ? rc : upload(ctx, ctx->inst_dt, idt.data(), idt.size());
+    rc = rc ? rc : upload(ctx, ctx->edge_off_dev, ctx->edge_off.data(), ctx->edge_off.size());
+    rc = rc ? rc : upload(ctx, ctx->m_rp, mrp.data(), mrp.size());
+    rc = rc ? rc : upload(ctx, ctx->m_row, mrow.data(), mrow.size());
+    rc = rc ? rc : upload(ctx, ctx->m_ci, mci.data(), mci.size());
+    rc = rc ? rc : upload(ctx, ctx->m_v, mv.data(), mv.size());
+    if (rc) return rc;
+    CK(cudaMemsetAsync(ctx->ifix, 0, sizeof(unsigned long long) * ctx->E, ctx->stream));
+    CK(cudaMemsetAsync(ctx->j, 0, sizeof(double) * ctx->E, ctx->stream));
+    CK(cudaMemsetAsync(ctx->r, 0, sizeof(double) * ctx->E, ctx->stream));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
+    ctx->unit_host.assign(n_inst, 0.0);
+    ctx->shift.assign(n_inst, 0);
+    CK(cudaStreamSynchronize(ctx->stream));
+    *out = holder.release();
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_load_particles(fetdpic_ctx *ctx, int inst, double q, double m, long long n,
+                                      const double *x, const double *u, const int *cell_hint)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    if (ctx->finalized) return ctx->fail(FETDPIC_ESTATE, "particles must be loaded before the first step");
+    if (inst < 0 || inst >= (int)ctx->mesh.size() || n < 0 || (n > 0 && (!x || !u)) || !(m > 0))
+        return ctx->fail(FETDPIC_EINVAL, "bad load arguments");
+    if (ctx->staged.size() >= 32767) return ctx->fail(FETDPIC_EINVAL, "too many species");
+    const HostMesh &M = ctx->mesh[inst];
+    StagedSpecies s;
+    s.inst = inst; s.q = q; s.m = m;
+    s.cell.resize(n); s.x.resize(n); s.y.resize(n); s.ux.resize(n); s.uy.resize(n);
+    for (long long k = 0; k < n; ++k) {
+        const int c = host_locate(M, x[2 * k], x[2 * k + 1], cell_hint ? cell_hint[k] : -1);
+        if (c < 0) return ctx->fail(FETDPIC_EOUTSIDE, "particle " + std::to_string(k) + " lies in no triangle");
+        if (!std::isfinite(u[2 * k]) || !std::isfinite(u[2 * k + 1]))
+            return ctx->fail(FETDPIC_ENONFINITE, "non-finite momentum at load");
+        s.cell[k] = c;
+        s.x[k] = x[2 * k]; s.y[k] = x[2 * k + 1];
+        s.ux[k] = u[2 * k]; s.uy[k] = u[2 * k + 1];
+    }
+    ctx->staged.push_back(std::move(s));
+    return (int)ctx->staged.size() - 1;
+}
+
+// Move the staged species to the device: padded species ranges, block ->
+// species table, fixed-point scale of the current per instance.
+static int finalize(fetdpic_ctx *ctx)
+{
+    if (ctx->finalized) return FETDPIC_OK;
+    const auto &P = ctx->p;
+    const int ni = (int)ctx->mesh.size();
+    const int ns = (int)ctx->staged.size();
+    // q_ref and the fixed-point shift per instance: the largest per-triangle
+    // charge weight sets the head room (x16 for clumping, crossings and the
+    // two triangles of an edge); shift <= 52 keeps the quantum at FP64 epsilon
+    // of one unit contribution.
+    std::vector<double> qref(ni, 0.0);
+    for (auto &s : ctx->staged) qref[s.inst] = std::max(qref[s.inst], std::fabs(s.q));
+    std::vector<std::vector<double>> wcell(ni);
+    for (int k = 0; k < ni; ++k) wcell[k].assign(ctx->mesh[k].nf, 0.0);
+    for (auto &s : ctx->staged) {
+        const double w = qref[s.inst] > 0 ? std::fabs(s.q) / qref[s.inst] : 0.0;
+        for (int c : s.cell) wcell[s.inst][c] += w;
+    }
+    for (int k = 0; k < ni; ++k) {
+        double wmax = 1.0;
+        for (double w : wcell[k]) wmax = std::max(wmax, w);
+        int sh = 62 - (int)std::ceil(std::log2(16.0 * wmax + 1.0));
+        sh = std::max(20, std::min(52, sh));
+        ctx->shift[k] = sh;
+        const double qr = qref[k] > 0 ? qref[k] : 1.0;
+        ctx->unit_host[k] = (qr / ctx->inst[k].dt) * std::ldexp(1.0, -sh);
+    }
+    ctx->sp.resize(ns);
+    long long off = 0, packed = 0, hist_n = 0;
+    std::vector<long long> pad_adj(ns);
+    std::vector<int> hoff(ns);
+    for (int s = 0; s < ns; ++s) {
+        const StagedSpecies &S = ctx->staged[s];
+        Species &D = ctx->sp[s];
+        std::memset(&D, 0, sizeof(D));
+        const fetdpic_instance &I = ctx->inst[S.inst];
+        const double dt = I.dt;
+        D.alpha = S.q * dt / (2.0 * S.m);
+        const double qr = qref[S.inst] > 0 ? qref[S.inst] : 1.0;
+        D.wfix = (S.q / qr) * std::ldexp(1.0, ctx->shift[S.inst]);
+        D.qfix = D.wfix;
+        D.wfix32 = (float)D.wfix;
+        D.dt = dt; D.c = P.c; D.ic2 = 1.0 / (P.c * P.c);
+        D.ext_ex = I.ext_ex; D.ext_ey = I.ext_ey; D.ext_bz = I.ext_bz;
+        D.kappa = (float)(S.q / S.m);
+        D.xe_x = (float)(S.q / S.m * dt / (2.0 * P.c) * I.ext_ex);
+        D.xe_y = (float)(S.q / S.m * dt / (2.0 * P.c) * I.ext_ey);
+        D.xb = (float)(S.q / S.m * dt / 2.0 * I.ext_bz);
+        D.inst = S.inst;
+        D.n = (long long)S.cell.size();
+        D.cap = ((D.n + SPECIES_ALIGN - 1) / SPECIES_ALIGN) * SPECIES_ALIGN;
+        D.off = off;
+        D.cell_off = ctx->cell_off[S.inst];
+        D.nf = ctx->mesh[S.inst].nf;
+        pad_adj[s] = off - packed;
+        hoff[s] = (int)hist_n;
+        hist_n += D.nf;
+        off += D.cap;
+        packed += D.n;
+    }
+    ctx->P = off;
+    ctx->nblocks = off / ctx->block;
+    ctx->hist_n = hist_n;
+    const bool f32 = P.precision == FETDPIC_FP32;
+    const size_t fb = f32 ? 4 : 8;
+    try {
+        ctx->sp_dev = ctx->alloc<Species>(std::max(ns, 1));
+        ctx->cell = ctx->alloc<int>(ctx->P);
+        ctx->cell_tmp = ctx->alloc<int>(ctx->P);
+        ctx->id = ctx->alloc<int>(ctx->P);
+        ctx->id_tmp = ctx->alloc<int>(ctx->P);
+        for (int k = 0; k < 4; ++k) {
+            ctx->f[k] = ctx->alloc<char>(fb * ctx->P);
+            ctx->f_tmp[k] = ctx->alloc<char>(fb * ctx->P);
+        }
+        ctx->blk_sp = ctx->alloc<short>(std::max<long long>(ctx->nblocks, 1));
+        ctx->hist = ctx->alloc<int>(std::max<long long>(hist_n, 1));
+        ctx->hoff = ctx->alloc<int>(std::max(ns, 1));
+        ctx->scan_tmp = ctx->alloc<int>(scan_tmp_ints(std::max<long long>(hist_n, 1)));
+        ctx->pad_adj = ctx->alloc<long long>(std::max(ns, 1));
+        if (P.record_walk > 0) {
+            ctx->rec_cnt = ctx->alloc<int>(ctx->P);
+            ctx->rec = ctx->alloc<int>((size_t)ctx->P * P.record_walk);
+        }
+    } catch (const std::bad_alloc &) {
+        return FETDPIC_ENOMEM;
+    }
+    // host images
+    std::vector<int> cell(ctx->P, -1), id(ctx->P, 0);
+    std::vector<char> fh[4];
+    for (int k = 0; k < 4; ++k) fh[k].assign(fb * ctx->P, 0);
+    std::vector<short> blk(ctx->nblocks);
+    for (int s = 0; s < ns; ++s) {
+        const StagedSpecies &S = ctx->staged[s];
+        const Species &D = ctx->sp[s];
+        const HostMesh &M = ctx->mesh[S.inst];
+        for (long long b = D.off / ctx->block; b < (D.off + D.cap) / ctx->block; ++b) blk[b] = (short)s;
+        for (long long k = 0; k < D.n; ++k) {
+            const long long q = D.off + k;
+            cell[q] = D.cell_off + S.cell[k];
+            id[q] = (int)k;
+            if (f32) {
+                double l[3];
+                host_lambdas(M, S.cell[k], S.x[k], S.y[k], l);
+                ((float *)fh[0].data())[q] = (float)l[0];
+                ((float *)fh[1].data())[q] = (float)l[1];
+                ((float *)fh[2].data())[q] = (float)(S.ux[k] / P.c);
+                ((float *)fh[3].data())[q] = (float)(S.uy[k] / P.c);
+            } else {
+                ((double *)fh[0].data())[q] = S.x[k];
+                ((double *)fh[1].data())[q] = S.y[k];
+                ((double *)fh[2].data())[q] = S.ux[k];
+                ((double *)fh[3].data())[q] = S.uy[k];
+            }
+        }
+    }
+    int rc = FETDPIC_OK;
+    rc = rc ? rc : upload(ctx, ctx->sp_dev, ctx->sp.data(), ctx->sp.size());
+    rc = rc ? rc : upload(ctx, ctx->cell, cell.data(), cell.size());
+    rc = rc ? rc : upload(ctx, ctx->cell_tmp, cell.data(), cell.size());   // padding stays -1 in both buffers
+    rc = rc ? rc : upload(ctx, ctx->id, id.data(), id.size());
+    for (int k = 0; k < 4; ++k) rc = rc ? rc : upload(ctx, (char *)ctx->f[k], fh[k].data(), fh[k].size());
+    rc = rc ? rc : upload(ctx, ctx->blk_sp, blk.data(), blk.size());
+    rc = rc ? rc : upload(ctx, ctx->hoff, hoff.data(), hoff.size());
+    rc = rc ? rc : upload(ctx, ctx->pad_adj, pad_adj.data(), pad_adj.size());
+    rc = rc ? rc : upload(ctx, ctx->inst_unit, ctx->unit_host.data(), ctx->unit_host.size());
+    if (rc) return rc;
+    if (ctx->rec_cnt) CK(cudaMemsetAsync(ctx->rec_cnt, 0, sizeof(int) * ctx->P, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->finalized = true;
+    return FETDPIC_OK;
+}
+
+static StepArgs64 args64(fetdpic_ctx *ctx)
+{
+    StepArgs64 a{};
+    a.geo = ctx->geo64; a.topo = ctx->topo; a.rec = ctx->rec64;
+    a.sp = ctx->sp_dev; a.blk_sp = ctx->blk_sp;
+    a.x = (double *)ctx->f[0]; a.y = (double *)ctx->f[1]; a.ux = (double *)ctx->f[2]; a.uy = (double *)ctx->f[3];
+    a.cell = ctx->cell;
+    a.ifix = ctx->ifix; a.status = ctx->status;
+    a.max_cross = ctx->p.max_crossings;
+    a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec;
+    a.edge_off = ctx->edge_off_dev;
+    a.nblocks = ctx->nblocks; a.block = ctx->block;
+    return a;
+}
+
+static StepArgs32 args32(fetdpic_ctx *ctx)
+{
+    StepArgs32 a{};
+    a.geo = ctx->geo32; a.topo = ctx->topo; a.rec = ctx->rec32;
+    a.sp = ctx->sp_dev; a.blk_sp = ctx->blk_sp;
+    a.l0 = (float *)ctx->f[0]; a.l1 = (float *)ctx->f[1]; a.ux = (float *)ctx->f[2]; a.uy = (float *)ctx->f[3];
+    a.cell = ctx->cell;
+    a.ifix = ctx->ifix; a.status = ctx->status;
+    a.max_cross = ctx->p.max_crossings;
+    a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec;
+    a.edge_off = ctx->edge_off_dev;
+    a.nblocks = ctx->nblocks; a.block = ctx->block;
+    return a;
+}
+
+static void mark(fetdpic_ctx *ctx, int stage)
+{
+    if (ctx->ev_used == (int)ctx->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        ctx->ev.push_back(e);
+        ctx->ev_stage.push_back(0);
+    }
+    cudaEventRecord(ctx->ev[ctx->ev_used], ctx->stream);
+    ctx->ev_stage[ctx->ev_used] = stage;
+    ++ctx->ev_used;
+}
+
+// Fold the recorded events into the per-stage sums (stream must be idle).
+static void collect_events(fetdpic_ctx *ctx)
+{
+    for (int k = 1; k < ctx->ev_used; ++k) {
+        const int sg = ctx->ev_stage[k];
+        if (sg < 0) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev[k - 1], ctx->ev[k]) == cudaSuccess) {
+            if (sg == 3) { ctx->stage_ms[2] += ms; ctx->stage_ms[3] += 1.0; }
+            else if (sg < 6) ctx->stage_ms[sg] += ms;
+        }
+    }
+    ctx->ev_used = 0;
+}
+
+static void do_sort(fetdpic_ctx *ctx)
+{
+    SortArgs s{};
+    s.nsp = (int)ctx->sp.size(); s.sp_dev = ctx->sp_dev; s.sp_host = ctx->sp.data();
+    s.P = ctx->P;
+    s.cell = ctx->cell; s.cell_tmp = ctx->cell_tmp; s.id = ctx->id; s.id_tmp = ctx->id_tmp;
+    for (int k = 0; k < 4; ++k) { s.f[k] = ctx->f[k]; s.f_tmp[k] = ctx->f_tmp[k]; }
+    s.fbytes = ctx->p.precision == FETDPIC_FP32 ? 4 : 8;
+    s.hist = ctx->hist; s.hoff = ctx->hoff; s.hist_n = ctx->hist_n; s.scan_tmp = ctx->scan_tmp;
+    s.pad_adj_dev = ctx->pad_adj; s.blk_sp = ctx->blk_sp; s.nblocks = ctx->nblocks; s.block = ctx->block;
+    launch_sort(ctx->stream, s);
+    std::swap(ctx->cell, ctx->cell_tmp);
+    std::swap(ctx->id, ctx->id_tmp);
+    for (int k = 0; k < 4; ++k) std::swap(ctx->f[k], ctx->f_tmp[k]);
+}
+
+// One time step: Faraday (+ field record), particles, Ampere, periodic sort.
+// `timed`: record stage events (time_stages = 1).
+static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
+{
+    long long launches = 0;
+    const bool f32 = ctx->p.precision == FETDPIC_FP32;
+    if (timed) mark(ctx, -1);
+    if (f32) launch_faraday32(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec32, ctx->p.c);
+    else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
+    launches += ctx->F > 0;
+    if (timed) mark(ctx, 0);
+    if (ctx->nblocks > 0) {
+        if (f32) launch_particles32(ctx->stream, pusher, args32(ctx));
+        else launch_particles64(ctx->stream, pusher, args64(ctx));
+        ++launches;
+    }
+    if (timed) mark(ctx, 1);
+    AmpereArgs A{};
+    A.E = ctx->E; A.efac = ctx->efac; A.ecoef = ctx->ecoef; A.einst = ctx->einst;
+    A.inst_unit = ctx->inst_unit; A.inst_dt = ctx->inst_dt; A.b = ctx->b; A.ifix = ctx->ifix;
+    A.r = ctx->r; A.d = ctx->d; A.j = ctx->j;
+    A.nfree = ctx->nfree; A.m_rp = ctx->m_rp; A.m_row = ctx->m_row; A.m_ci = ctx->m_ci; A.m_v = ctx->m_v;
+    A.e = ctx->e;
+    launch_ampere(ctx->stream, A);
+    launches += (ctx->E > 0) + (ctx->nfree > 0);
+    if (timed) mark(ctx, 3);
+    ++ctx->steps_done;
+    if (ctx->p.sort_interval > 0 && ctx->nblocks > 0 && ctx->steps_done % ctx->p.sort_interval == 0) {
+        do_sort(ctx);
+        launches += 5;
+        if (timed) mark(ctx, 4);
+    }
+    return launches;
+}
+
+extern "C" int fetdpic_step(fetdpic_ctx *ctx, long long nsteps, int pusher)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    if (nsteps < 0 || pusher < 0 || pusher > 3) return ctx->fail(FETDPIC_EINVAL, "bad step arguments");
+    int rc = finalize(ctx);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    // keep the event pool bounded: fold what an earlier call recorded first
+    if (ctx->ev_used > 0 && ctx->ev_used + 8 * nsteps > 4096) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        collect_events(ctx);
+    }
+    long long launches = 0;
+    const bool timed = ctx->p.time_stages != 0;
+    for (long long s = 0; s < nsteps; ++s) {
+        if (timed && ctx->ev_used > 4000) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            collect_events(ctx);
+        }
+        launches += enqueue_step(ctx, pusher, timed);
+    }
+    ctx->launches_acc += launches;
+    CK(cudaGetLastError());
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_sync(fetdpic_ctx *ctx)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned st = 0;
+    if (ctx->status) CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    collect_events(ctx);
+    return map_status(ctx, st);
+}
+
+// Reusable device scratch for particle-state transfers (grown on demand).
+static void *xfer_buf(fetdpic_ctx *ctx, size_t bytes)
+{
+    if (bytes <= ctx->xfer_bytes) return ctx->xfer;
+    if (ctx->xfer) {
+        for (size_t k = 0; k < ctx->allocs.size(); ++k)
+            if (ctx->allocs[k] == ctx->xfer) { ctx->allocs.erase(ctx->allocs.begin() + k); break; }
+        if (ctx->p.dev_free) ctx->p.dev_free(ctx->xfer, ctx->p.alloc_user);
+        else cudaFree(ctx->xfer);
+        ctx->xfer = nullptr; ctx->xfer_bytes = 0;
+    }
+    try { ctx->xfer = ctx->alloc<char>(bytes); } catch (const std::bad_alloc &) { return nullptr; }
+    ctx->xfer_bytes = bytes;
+    return ctx->xfer;
+}
+
+extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const double *x, const double *u, const int *cell)
+{
+    if (!ctx || species < 0) return FETDPIC_EINVAL;
+    int rc = finalize(ctx);
+    if (rc) return rc;
+    if (species >= (int)ctx->sp.size() || (!x && ctx->sp[species].n) || (!u && ctx->sp[species].n))
+        return ctx->fail(FETDPIC_EINVAL, "bad species or buffers");
+    const Species &D = ctx->sp[species];
+    const HostMesh &M = ctx->mesh[D.inst];
+    if (D.n == 0) return FETDPIC_OK;
+    std::vector<int> located;
+    const int *cl = cell;
+    if (!cl) {
+        located.resize(D.n);
+        for (long long k = 0; k < D.n; ++k) {
+            located[k] = host_locate(M, x[2 * k], x[2 * k + 1], -1);
+            if (located[k] < 0) return ctx->fail(FETDPIC_EOUTSIDE, "particle outside the mesh");
+        }
+        cl = located.data();
+    } else {
+        for (long long k = 0; k < D.n; ++k)
+            if (cl[k] < 0 || cl[k] >= M.nf) return ctx->fail(FETDPIC_EINVAL, "cell index out of range");
+    }
+    // staging: x [n][2], u [n][2] (FP64), cell [n]
+    const size_t bx = sizeof(double) * 2 * D.n, bc = sizeof(int) * D.n;
+    char *st = (char *)xfer_buf(ctx, 2 * bx + bc);
+    if (!st) return FETDPIC_ENOMEM;
+    CK(cudaMemcpyAsync(st, x, bx, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(st + bx, u, bx, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(st + 2 * bx, cl, bc, cudaMemcpyHostToDevice, ctx->stream));
+    launch_ingest(ctx->stream, D.n, D.off, D.cell_off, ctx->p.precision == FETDPIC_FP32,
+                  (const double *)st, (const double *)(st + bx), (const int *)(st + 2 * bx), ctx->geo64,
+                  1.0 / ctx->p.c, ctx->cell, ctx->id, ctx->f[0], ctx->f[1], ctx->f[2], ctx->f[3]);
+    CK(cudaGetLastError());
+    if (!cell) CK(cudaStreamSynchronize(ctx->stream));   // `located` goes out of scope
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_write_fields(fetdpic_ctx *ctx, int inst, const double *e, const double *b)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    const HostMesh &M = ctx->mesh[inst];
+    if (e) {
+        std::vector<double> ev(e, e + M.ne);
+        for (int k = 0; k < M.ne; ++k) if (M.pec[k]) ev[k] = 0.0;
+        int rc = upload(ctx, ctx->e + ctx->edge_off[inst], ev.data(), ev.size());
+        if (rc) return rc;
+        // restart the dual flux consistently: d = [*eps] e
+        std::vector<double> dv(M.ne, 0.0);
+        for (int k = 0; k < M.ne; ++k)
+            for (long long q = M.h_rp[k]; q < M.h_rp[k + 1]; ++q) dv[k] += M.h_v[q] * ev[M.h_ci[q]];
+        rc = upload(ctx, ctx->d + ctx->edge_off[inst], dv.data(), dv.size());
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    if (b) {
+        int rc = upload(ctx, ctx->b + ctx->cell_off[inst], b, (size_t)M.nf);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
+                            int species, double *x, double *u, int *cell)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    const HostMesh &M = ctx->mesh[inst];
+    if (e) CK(cudaMemcpyAsync(e, ctx->e + ctx->edge_off[inst], sizeof(double) * M.ne, cudaMemcpyDeviceToHost, ctx->stream));
+    if (b) CK(cudaMemcpyAsync(b, ctx->b + ctx->cell_off[inst], sizeof(double) * M.nf, cudaMemcpyDeviceToHost, ctx->stream));
+    if (j) CK(cudaMemcpyAsync(j, ctx->j + ctx->edge_off[inst], sizeof(double) * M.ne, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (x || u || cell) {
+        int rc = finalize(ctx);
+        if (rc) return rc;
+        if (species < 0 || species >= (int)ctx->sp.size()) return ctx->fail(FETDPIC_EINVAL, "bad species");
+        const Species &D = ctx->sp[species];
+        if (D.n > 0) {
+            const size_t bx = sizeof(double) * 2 * D.n, bc = sizeof(int) * D.n;
+            char *st = (char *)xfer_buf(ctx, 2 * bx + bc);
+            if (!st) return FETDPIC_ENOMEM;
+            double *ox = (double *)st, *ou = (double *)(st + bx);
+            int *oc = (int *)(st + 2 * bx);
+            if (ctx->p.precision == FETDPIC_FP32)
+                launch_unsort32(ctx->stream, ctx->P, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
+                                (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap,
+                                D.cell_off, ox, ou, oc);
+            else
+                launch_unsort64(ctx->stream, ctx->P, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
+                                (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, D.cell_off, ox, ou, oc);
+            CK(cudaGetLastError());
+            if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->stream));
+            if (u) CK(cudaMemcpyAsync(u, ou, bx, cudaMemcpyDeviceToHost, ctx->stream));
+            if (cell) CK(cudaMemcpyAsync(cell, oc, bc, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
+    unsigned st = 0;
+    if (ctx->status) CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return map_status(ctx, st);
+}
+
+extern "C" int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *rec)
+{
+    if (!ctx || !cnt || !rec) return FETDPIC_EINVAL;
+    if (ctx->p.record_walk <= 0) return ctx->fail(FETDPIC_ESTATE, "record_walk is off");
+    int rc = finalize(ctx);
+    if (rc) return rc;
+    if (species < 0 || species >= (int)ctx->sp.size()) return FETDPIC_EINVAL;
+    const Species &D = ctx->sp[species];
+    if (D.n == 0) return FETDPIC_OK;
+    int *oc = nullptr, *orc = nullptr;
+    try {
+        oc = ctx->alloc<int>(D.n);
+        orc = ctx->alloc<int>((size_t)D.n * ctx->p.record_walk);
+    } catch (const std::bad_alloc &) {
+        return FETDPIC_ENOMEM;
+    }
+    launch_unsort_rec(ctx->stream, D.off, D.cap, ctx->id, ctx->cell, ctx->rec_cnt, ctx->rec, ctx->p.record_walk, oc, orc);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(cnt, oc, sizeof(int) * D.n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rec, orc, sizeof(int) * D.n * ctx->p.record_walk, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 2; ++k) {
+        void *q = ctx->allocs.back();
+        ctx->allocs.pop_back();
+        if (ctx->p.dev_free) ctx->p.dev_free(q, ctx->p.alloc_user);
+        else cudaFree(q);
+    }
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double *dgl_max, double *energy)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    (void)dce_max; (void)dgl_max; (void)energy;
+    return ctx->fail(FETDPIC_ESTATE, "checks are not enabled in this build");
+}
+
+extern "C" int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6])
+{
+    if (!ctx || !out || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    const HostMesh &M = ctx->mesh[inst];
+    out[0] = M.nn; out[1] = M.ne; out[2] = M.nf; out[3] = (long long)M.free_edges.size();
+    out[4] = M.m_rp.empty() ? 0 : M.m_rp.back();
+    long long np = 0;
+    for (auto &s : ctx->staged) if (s.inst == inst) np += (long long)s.cell.size();
+    out[5] = np;
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_read_edges(fetdpic_ctx *ctx, int inst, int *edges)
+{
+    if (!ctx || !edges || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    const HostMesh &M = ctx->mesh[inst];
+    std::memcpy(edges, M.edge.data(), sizeof(int) * M.edge.size());
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_edge, int *col, double *val)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    const HostMesh &M = ctx->mesh[inst];
+    if (rowptr) std::memcpy(rowptr, M.m_rp.data(), sizeof(long long) * M.m_rp.size());
+    if (row_edge) std::memcpy(row_edge, M.free_edges.data(), sizeof(int) * M.free_edges.size());
+    if (col) std::memcpy(col, M.m_ci.data(), sizeof(int) * M.m_ci.size());
+    if (val) std::memcpy(val, M.m_v.data(), sizeof(double) * M.m_v.size());
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_stage_times(fetdpic_ctx *ctx, double out[6], long long *launches)
+{
+    if (!ctx || !out) return FETDPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    collect_events(ctx);
+    for (int k = 0; k < 6; ++k) { out[k] = ctx->stage_ms[k]; ctx->stage_ms[k] = 0.0; }
+    if (launches) *launches = ctx->launches_acc;
+    ctx->launches_acc = 0;
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_particle_bytes(fetdpic_ctx *ctx, double *bytes, long long *n_particles)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    long long n = 0;
+    for (auto &s : ctx->sp) n += s.n;
+    if (!ctx->finalized) for (auto &s : ctx->staged) n += (long long)s.cell.size();
+    // per particle-step: state in + out (cell 4 B + 4 values); see the design notes
+    const double per = ctx->p.precision == FETDPIC_FP32 ? 2.0 * (4 + 4 * 4) : 2.0 * (4 + 4 * 8);
+    if (bytes) *bytes = per * (double)n;
+    if (n_particles) *n_particles = n;
+    return FETDPIC_OK;
+}
+
+extern "C" const char *fetdpic_last_error(const fetdpic_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "null context";
+}
+
+extern "C" void fetdpic_destroy(fetdpic_ctx *ctx)
+{
+    delete ctx;
+}

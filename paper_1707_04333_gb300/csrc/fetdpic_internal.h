@@ -1,0 +1,184 @@
+// Internal declarations of the fetdpic library (host setup, device records,
+// kernel launchers).  Not part of the public C ABI (include/fetdpic.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/fetdpic.h"
+
+namespace fetdpic {
+
+// ------------------------------------------------------------ host setup
+
+// One mesh instance after validation: counter-clockwise triangles, edge
+// numbering, incidence (Sec. II.A), Whitney geometry and matrices.
+struct HostMesh {
+    int nn = 0, nf = 0, ne = 0;
+    std::vector<double> xy;                 // [nn][2]
+    std::vector<int> tri;                   // [nf][3] CCW
+    std::vector<int> edge;                  // [ne][2] orientation i -> j
+    std::vector<int> tedge, tsign;          // [nf][3] edge of local edge m, +-1
+    std::vector<int> tnb, tnbm;             // [nf][3] neighbour triangle / its local edge index, -1 at walls
+    std::vector<char> pec;                  // [ne] e held at 0
+    std::vector<int> efac;                  // [ne][2] adjacent triangles (second = -1 on walls)
+    std::vector<int> efsign;                // [ne][2] circulation sign of the edge in each triangle
+    std::vector<double> d2A, inv2A;         // [nf]
+    std::vector<double> gx, gy, X, Y;       // [nf][3] grad lambda_m, node coordinates
+    // [*eps] restricted to free edges, CSR over free-edge indices
+    std::vector<int> free_edges;            // ascending edge ids
+    std::vector<long long> a_rp; std::vector<int> a_ci; std::vector<double> a_v;
+    // full [*eps] over all edges (for d^0 = [*eps] e^0 and the field energy)
+    std::vector<long long> h_rp; std::vector<int> h_ci; std::vector<double> h_v;
+    // SPAI M ~ [*eps]^-1, CSR with free-edge rows and edge-id columns
+    std::vector<long long> m_rp; std::vector<int> m_ci; std::vector<double> m_v;
+};
+
+// Returns 0 or a negative fetdpic_status; msg gets a reason on error.
+int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri,
+               int ne_in, const int *edges_in, const int *tags_in, std::string &msg);
+int build_hodge(HostMesh &M, double eps0, std::string &msg);
+int build_spai(HostMesh &M, int level, std::string &msg);
+
+// Same barycentric evaluation the kernels use (gradient form, no FMA).
+void host_lambdas(const HostMesh &M, int f, double x, double y, double *l);
+int host_locate(const HostMesh &M, double x, double y, int hint);
+
+// --------------------------------------------------------- device records
+
+// FP64 geometry of one triangle: lambda_m(r) = gx_m (x - X_{m+1}) + gy_m (y - Y_{m+1}).
+struct __align__(16) Geo64 {
+    double gx[3], gy[3], X[3], Y[3];
+    double inv2A, dt, hb, pad;              // hb = 1/(mu0 A): diagonal [*mu^-1]
+};
+static_assert(sizeof(Geo64) == 128, "Geo64 layout");
+
+// FP32 geometry: G_m = c dt grad lambda_m (dimensionless step in barycentrics per unit v/c).
+struct __align__(16) Geo32 {
+    float G[6];                             // (G0x, G0y, G1x, G1y, G2x, G2y)
+    float pad[2];
+};
+
+// Topology: edge word = (global edge << 1) | (sign < 0); neighbour word =
+// (global triangle << 2) | local index of the shared edge there, -1 on a wall.
+struct __align__(16) Topo {
+    int ew[3];
+    int nb[3];
+    int node[3];
+    int inst;
+};
+static_assert(sizeof(Topo) == 48, "Topo layout");
+
+// Fields seen by the particles of one triangle at step n (written by the
+// Faraday kernel): FP64 path: (s_m e_m for m = 0..2, B_z^n); FP32 path:
+// E(lambda) = sum_n lambda_n V_n scaled by dt/(2c), B_z scaled by dt/2.
+struct __align__(32) Rec64 { double se[3]; double bz; };
+struct __align__(32) Rec32 { float v[6]; float bz; float pad; };
+
+struct Species {
+    double alpha;                           // q dt / (2 m)
+    double wfix;                            // (q / q_ref) * 2^shift: deposit weight in fixed point
+    double qfix;                            // same for the nodal charge
+    double dt, c, ic2;
+    double ext_ex, ext_ey, ext_bz;
+    float kappa;                            // q/m (FP32 path)
+    float xe_x, xe_y, xb;                   // external fields pre-scaled for the FP32 path
+    float wfix32;
+    int inst;
+    int pad_;
+    long long off, n, cap;                  // storage range [off, off+cap), n live
+    int cell_off, nf;                       // triangle range of the instance
+};
+
+enum StatusBits : unsigned {
+    ST_WALK = 1u, ST_NONFINITE = 2u, ST_MESH = 4u
+};
+
+// ----------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return immediately.
+
+struct StepArgs64 {
+    const Geo64 *geo; const Topo *topo; const Rec64 *rec;
+    const Species *sp; const short *blk_sp;
+    double *x, *y, *ux, *uy; int *cell;
+    unsigned long long *ifix;               // [E] fixed-point current (two's complement)
+    unsigned *status;
+    int max_cross;
+    int rec_cap; int *rec_cnt; int *wrec;   // walk record (rec_cap = 0: off)
+    const int *edge_off;                    // per instance, for instance-local record ids
+    long long nblocks; int block;
+};
+
+struct StepArgs32 {
+    const Geo32 *geo; const Topo *topo; const Rec32 *rec;
+    const Species *sp; const short *blk_sp;
+    float *l0, *l1, *ux, *uy; int *cell;
+    unsigned long long *ifix;
+    unsigned *status;
+    int max_cross;
+    int rec_cap; int *rec_cnt; int *wrec;
+    const int *edge_off;
+    long long nblocks; int block;
+};
+
+void launch_faraday64(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
+                      double *b, Rec64 *rec);
+void launch_faraday32(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
+                      double *b, Rec32 *rec, double c);
+void launch_particles64(cudaStream_t st, int pusher, const StepArgs64 &a);
+void launch_particles32(cudaStream_t st, int pusher, const StepArgs32 &a);
+
+struct AmpereArgs {
+    int E;
+    const int2 *efac; const double2 *ecoef;  // adjacent triangles, s_f / (mu0 A_f)
+    const int *einst;                         // instance of each edge
+    const double *inst_unit;                  // (q_ref/dt) 2^-shift per instance
+    const double *inst_dt;
+    const double *b;
+    unsigned long long *ifix;                 // read and cleared
+    double *r, *d, *j;
+    long long nfree;
+    const long long *m_rp; const int *m_row; const int *m_ci; const double *m_v;  // dt-scaled SPAI
+    double *e;
+};
+void launch_ampere(cudaStream_t st, const AmpereArgs &a);
+
+// Counting sort of particles by triangle, per species range.
+struct SortArgs {
+    int nsp; const Species *sp_dev; const Species *sp_host;
+    long long P;                              // storage size (padded)
+    int *cell; int *cell_tmp;
+    int *id; int *id_tmp;
+    void *f[4]; void *f_tmp[4]; int fbytes;   // four payload arrays of fbytes each
+    int *hist;                                // sum over species of nf (+1)
+    int *hoff;                                // per species offset into hist
+    long long hist_n;
+    int *scan_tmp;                            // scratch for the block sums
+    const long long *pad_adj_dev;             // per species storage_off - packed_off
+    const short *blk_sp; long long nblocks; int block;
+};
+void launch_sort(cudaStream_t st, const SortArgs &a);
+
+
+size_t scan_tmp_ints(long long n);
+void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n, int *tmp);
+
+// Host-layout particle state into a species range (FP32: barycentrics, u/c).
+void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, bool fp32, const double *x,
+                   const double *u, const int *cell, const Geo64 *geo, double inv_c, int *cell_o, int *id_o,
+                   void *f0, void *f1, void *f2, void *f3);
+
+// Particle state to load order (FP32 converts barycentrics to coordinates).
+void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
+                     const double *y, const double *ux, const double *uy, long long off, long long cap,
+                     int cell_off, double *ox, double *ou, int *oc);
+void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
+                     const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
+                     long long off, long long cap, int cell_off, double *ox, double *ou, int *oc);
+void launch_unsort_rec(cudaStream_t st, long long off, long long cap, const int *id, const int *cell,
+                       const int *cnt, const int *rec, int rec_cap, int *ocnt, int *orec);
+
+}  // namespace fetdpic

@@ -1,0 +1,331 @@
+// Field-update (Ampere) kernels, the counting sort of particles by triangle,
+// the scan it needs, and the kernels that return particles in load order.
+#include <cuda_runtime.h>
+
+#include "fetdpic_internal.h"
+
+namespace fetdpic {
+
+// r = C^T [*mu^-1] b^{n+1/2} - i^{n+1/2} on every edge (Eq. (semi.dis.curl.2)),
+// with [*mu^-1] = 1/(mu0 A_f) folded into ecoef = s_f/(mu0 A_f).  The
+// fixed-point current is converted (unit = (q_ref/dt) 2^-shift per
+// instance), kept in j for reading, and cleared for the next step.  The dual
+// flux d += dt r accumulates for the Gauss-law check.
+__global__ void k_curl_h(int E, const int2 *__restrict__ efac, const double2 *__restrict__ ecoef,
+                         const int *__restrict__ einst, const double *__restrict__ unit,
+                         const double *__restrict__ idt, const double *__restrict__ b,
+                         unsigned long long *__restrict__ ifix, double *__restrict__ r,
+                         double *__restrict__ d, double *__restrict__ j)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int2 fa = efac[e];
+    const double2 cf = ecoef[e];
+    double h = b[fa.x] * cf.x;
+    if (fa.y >= 0) h += b[fa.y] * cf.y;
+    const int in = einst[e];
+    const long long iv = (long long)ifix[e];
+    ifix[e] = 0ull;
+    const double cur = (double)iv * unit[in];
+    const double rv = h - cur;
+    r[e] = rv;
+    j[e] = cur;
+    d[e] += idt[in] * rv;
+}
+
+// e_free += (dt M) r: SpMV with the dt-scaled SPAI, 8 lanes per row.
+__global__ void k_spai_spmv(long long nrows, const long long *__restrict__ rp, const int *__restrict__ row_edge,
+                            const int *__restrict__ ci, const double *__restrict__ v,
+                            const double *__restrict__ r, double *__restrict__ e)
+{
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long row = gid >> 3;
+    const int sub = threadIdx.x & 7;
+    double s = 0.0;
+    if (row < nrows) {
+        const long long lo = rp[row], hi = rp[row + 1];
+        for (long long q = lo + sub; q < hi; q += 8) s += v[q] * r[ci[q]];
+    }
+    s += __shfl_down_sync(0xffffffffu, s, 4, 8);
+    s += __shfl_down_sync(0xffffffffu, s, 2, 8);
+    s += __shfl_down_sync(0xffffffffu, s, 1, 8);
+    if (row < nrows && sub == 0) e[row_edge[row]] += s;
+}
+
+void launch_ampere(cudaStream_t st, const AmpereArgs &a)
+{
+    if (a.E > 0)
+        k_curl_h<<<(a.E + 255) / 256, 256, 0, st>>>(a.E, a.efac, a.ecoef, a.einst, a.inst_unit, a.inst_dt,
+                                                     a.b, a.ifix, a.r, a.d, a.j);
+    if (a.nfree > 0) {
+        const long long threads = a.nfree * 8;
+        k_spai_spmv<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a.nfree, a.m_rp, a.m_row, a.m_ci, a.m_v,
+                                                                       a.r, a.e);
+    }
+}
+
+// ------------------------------------------------------------------- scan
+// Exclusive scan of n ints: per-block sums, a scan of the sums, block scans.
+
+constexpr int SCAN_B = 1024;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *sh, int &total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const int before = (w > 0 ? sh[w - 1] : 0) + x - v;
+    total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return before;
+}
+
+__global__ void k_scan_sums(const int *__restrict__ in, long long n, int *__restrict__ sums)
+{
+    __shared__ int sh[32];
+    const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    int tot;
+    block_exclusive_scan(v, sh, tot);
+    if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_single(int *__restrict__ sums, long long nb)
+{
+    // one block scans all block sums in chunks (nb is small: n / 1024)
+    __shared__ int sh[32];
+    int carry = 0;
+    for (long long base = 0; base < nb; base += SCAN_B) {
+        const long long i = base + threadIdx.x;
+        const int v = i < nb ? sums[i] : 0;
+        int tot;
+        const int ex = block_exclusive_scan(v, sh, tot);
+        if (i < nb) sums[i] = ex + carry;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_apply(const int *__restrict__ in, long long n, const int *__restrict__ sums, int *__restrict__ out)
+{
+    __shared__ int sh[32];
+    const long long i = (long long)blockIdx.x * SCAN_B + threadIdx.x;
+    const int v = i < n ? in[i] : 0;
+    int tot;
+    const int ex = block_exclusive_scan(v, sh, tot);
+    if (i < n) out[i] = ex + sums[blockIdx.x];
+}
+
+size_t scan_tmp_ints(long long n) { return (size_t)((n + SCAN_B - 1) / SCAN_B) + 1; }
+
+void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n, int *tmp)
+{
+    if (n <= 0) return;
+    const long long nb = (n + SCAN_B - 1) / SCAN_B;
+    k_scan_sums<<<(unsigned)nb, SCAN_B, 0, st>>>(in, n, tmp);
+    k_scan_single<<<1, SCAN_B, 0, st>>>(tmp, nb);
+    k_scan_apply<<<(unsigned)nb, SCAN_B, 0, st>>>(in, n, tmp, out);
+}
+
+// ------------------------------------------------------------------- sort
+// Counting sort by triangle within each species range: histogram (integer
+// atomics), exclusive scan, scatter through per-triangle cursors.  The order
+// of particles inside one triangle depends on atomic order; nothing computed
+// depends on it (the deposit is integer, reads go through the id array).
+
+__global__ void k_hist(const int *__restrict__ cell, const short *__restrict__ blk_sp, const Species *__restrict__ sp,
+                       const int *__restrict__ hoff, int *__restrict__ hist)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = cell[p];
+    if (c < 0) return;
+    const int s = blk_sp[blockIdx.x];
+    atomicAdd(hist + hoff[s] + (c - sp[s].cell_off), 1);
+}
+
+template <int FB>
+__global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ id,
+                          const short *__restrict__ blk_sp, const Species *__restrict__ sp,
+                          const int *__restrict__ hoff, int *__restrict__ cursor,
+                          const long long *__restrict__ pad_adj,
+                          const void *f0, const void *f1, const void *f2, const void *f3,
+                          int *__restrict__ cell_o, int *__restrict__ id_o,
+                          void *g0, void *g1, void *g2, void *g3)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = cell[p];
+    if (c < 0) return;
+    const int s = blk_sp[blockIdx.x];
+    const int slot = hoff[s] + (c - sp[s].cell_off);
+    // warp-aggregated cursor increments for particles of the same triangle
+    const unsigned peers = __match_any_sync(__activemask(), slot);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
+    int base = 0;
+    if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(cursor + slot, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const long long q = (long long)(base + rank) + pad_adj[s];
+    cell_o[q] = c;
+    id_o[q] = id[p];
+    using T = typename std::conditional<FB == 8, double, float>::type;
+    ((T *)g0)[q] = ((const T *)f0)[p];
+    ((T *)g1)[q] = ((const T *)f1)[p];
+    ((T *)g2)[q] = ((const T *)f2)[p];
+    ((T *)g3)[q] = ((const T *)f3)[p];
+}
+
+void launch_sort(cudaStream_t st, const SortArgs &a)
+{
+    cudaMemsetAsync(a.hist, 0, sizeof(int) * a.hist_n, st);
+    k_hist<<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.blk_sp, a.sp_dev, a.hoff, a.hist);
+    // exclusive scan in place into the cursor array (hist doubles as cursor)
+    launch_exclusive_scan(st, a.hist, a.hist, a.hist_n, a.scan_tmp);
+    if (a.fbytes == 8)
+        k_scatter<8><<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.id, a.blk_sp, a.sp_dev, a.hoff, a.hist,
+                                                              a.pad_adj_dev, a.f[0], a.f[1], a.f[2], a.f[3],
+                                                              a.cell_tmp, a.id_tmp, a.f_tmp[0], a.f_tmp[1],
+                                                              a.f_tmp[2], a.f_tmp[3]);
+    else
+        k_scatter<4><<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.id, a.blk_sp, a.sp_dev, a.hoff, a.hist,
+                                                              a.pad_adj_dev, a.f[0], a.f[1], a.f[2], a.f[3],
+                                                              a.cell_tmp, a.id_tmp, a.f_tmp[0], a.f_tmp[1],
+                                                              a.f_tmp[2], a.f_tmp[3]);
+}
+
+// ------------------------------------------------------------ load order
+
+// Host-layout particle state (x, u in FP64, instance-local cell) into the
+// storage range of one species, in load order.  FP32 storage gets the
+// barycentric coordinates of x in its triangle and u/c.
+__global__ void k_ingest(long long n, long long off, int cell_off, int fp32, const double *__restrict__ x,
+                         const double *__restrict__ u, const int *__restrict__ cell, const Geo64 *__restrict__ geo,
+                         double inv_c, int *__restrict__ cell_o, int *__restrict__ id_o, void *f0, void *f1,
+                         void *f2, void *f3)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long p = off + k;
+    const int c = cell_off + cell[k];
+    cell_o[p] = c;
+    id_o[p] = (int)k;
+    const double px = x[2 * k], py = x[2 * k + 1];
+    if (fp32) {
+        const Geo64 &G = geo[c];
+        const double l0 = G.gx[0] * (px - G.X[1]) + G.gy[0] * (py - G.Y[1]);
+        const double l1 = G.gx[1] * (px - G.X[2]) + G.gy[1] * (py - G.Y[2]);
+        ((float *)f0)[p] = (float)l0;
+        ((float *)f1)[p] = (float)l1;
+        ((float *)f2)[p] = (float)(u[2 * k] * inv_c);
+        ((float *)f3)[p] = (float)(u[2 * k + 1] * inv_c);
+    } else {
+        ((double *)f0)[p] = px;
+        ((double *)f1)[p] = py;
+        ((double *)f2)[p] = u[2 * k];
+        ((double *)f3)[p] = u[2 * k + 1];
+    }
+}
+
+void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, bool fp32, const double *x,
+                   const double *u, const int *cell, const Geo64 *geo, double inv_c, int *cell_o, int *id_o,
+                   void *f0, void *f1, void *f2, void *f3)
+{
+    if (n <= 0) return;
+    k_ingest<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, cell_off, fp32 ? 1 : 0, x, u, cell, geo, inv_c,
+                                                          cell_o, id_o, f0, f1, f2, f3);
+}
+
+__global__ void k_unsort64(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,
+                           const double *__restrict__ x, const double *__restrict__ y,
+                           const double *__restrict__ ux, const double *__restrict__ uy, int cell_off,
+                           double *__restrict__ ox, double *__restrict__ ou, int *__restrict__ oc)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cap) return;
+    const long long p = off + k;
+    const int c = cell[p];
+    if (c < 0) return;
+    const long long i = id[p];
+    if (ox) { ox[2 * i] = x[p]; ox[2 * i + 1] = y[p]; }
+    if (ou) { ou[2 * i] = ux[p]; ou[2 * i + 1] = uy[p]; }
+    if (oc) oc[i] = c - cell_off;
+}
+
+__global__ void k_unsort32(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,
+                           const float *__restrict__ l0, const float *__restrict__ l1,
+                           const float *__restrict__ ux, const float *__restrict__ uy,
+                           const Geo64 *__restrict__ geo, double c, int cell_off,
+                           double *__restrict__ ox, double *__restrict__ ou, int *__restrict__ oc)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cap) return;
+    const long long p = off + k;
+    const int f = cell[p];
+    if (f < 0) return;
+    const long long i = id[p];
+    if (ox) {
+        const double a = l0[p], b = l1[p];
+        const double cc = 1.0 - a - b;
+        const Geo64 &G = geo[f];
+        ox[2 * i] = a * G.X[0] + b * G.X[1] + cc * G.X[2];
+        ox[2 * i + 1] = a * G.Y[0] + b * G.Y[1] + cc * G.Y[2];
+    }
+    if (ou) { ou[2 * i] = (double)ux[p] * c; ou[2 * i + 1] = (double)uy[p] * c; }
+    if (oc) oc[i] = f - cell_off;
+}
+
+__global__ void k_unsort_rec(long long off, long long cap, const int *__restrict__ id, const int *__restrict__ cell,
+                             const int *__restrict__ cnt, const int *__restrict__ rec, int rc,
+                             int *__restrict__ ocnt, int *__restrict__ orec)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cap) return;
+    const long long p = off + k;
+    if (cell[p] < 0) return;
+    const long long i = id[p];
+    ocnt[i] = cnt[p];
+    for (int q = 0; q < rc; ++q) orec[i * rc + q] = rec[p * rc + q];
+}
+
+void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
+                     const double *y, const double *ux, const double *uy, long long off, long long cap,
+                     int cell_off, double *ox, double *ou, int *oc)
+{
+    (void)P;
+    if (cap <= 0) return;
+    k_unsort64<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, x, y, ux, uy, cell_off, ox, ou, oc);
+}
+
+void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
+                     const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
+                     long long off, long long cap, int cell_off, double *ox, double *ou, int *oc)
+{
+    (void)P;
+    if (cap <= 0) return;
+    k_unsort32<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, l0, l1, ux, uy, geo, c, cell_off,
+                                                              ox, ou, oc);
+}
+
+void launch_unsort_rec(cudaStream_t st, long long off, long long cap, const int *id, const int *cell,
+                        const int *cnt, const int *rec, int rec_cap, int *ocnt, int *orec)
+{
+    if (cap <= 0) return;
+    k_unsort_rec<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, id, cell, cnt, rec, rec_cap, ocnt, orec);
+}
+
+}  // namespace fetdpic

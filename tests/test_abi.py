@@ -1,0 +1,42 @@
+"""The C-ABI library loads and exports every symbol the public header declares (CPU only:
+no compute call is made)."""
+import ctypes
+import subprocess
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def libmod():
+    from paper_1707_04333_gb300 import build_lib, fetdpic
+    build_lib.build()
+    return fetdpic
+
+
+def test_header_symbols_exported(libmod):
+    syms = libmod.declared_symbols()
+    assert "fetdpic_create" in syms and "fetdpic_step" in syms and len(syms) >= 15
+    L = libmod.lib()
+    for s in syms:
+        assert hasattr(L, s), s
+    out = subprocess.run(["nm", "-D", "--defined-only", libmod.library_path()], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert set(syms) <= exported
+
+
+def test_kernels_target_sm103a(libmod):
+    """The library embeds sm_103a device code (checked from the build command, not the binary)."""
+    from paper_1707_04333_gb300 import build_lib
+    assert build_lib.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "-fmad=false" in build_lib.CU_SOURCES["kernels_fp64.cu"]
+
+
+def test_invalid_arguments_rejected_without_gpu(libmod):
+    """Argument validation happens before any device work."""
+    L = libmod.lib()
+    h = ctypes.c_void_p()
+    assert L.fetdpic_create(ctypes.byref(h), None, 1, None) == libmod.EINVAL
+    assert L.fetdpic_create(None, None, 0, None) == libmod.EINVAL
+    assert L.fetdpic_step(None, 1, 0) == libmod.EINVAL
+    assert L.fetdpic_sync(None) == libmod.EINVAL
+    assert L.fetdpic_last_error(None) == b"null context"
