@@ -169,6 +169,28 @@ int fetdpic_sync(fetdpic_ctx *ctx);
 int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
                  int species, double *x, double *u, int *cell);
 
+/* Same particle output as fetdpic_read (x, u, cell of species `species`, load
+ * order, FP32 positions converted), for callers that cannot allocate device
+ * memory at the time of the call: code running while a stream is being
+ * captured (allocation calls are not allowed there), real-time loops that
+ * forbid allocator latency, plug-ins whose host framework owns all device
+ * memory.  fetdpic_read allocates its device staging buffer on first use;
+ * this call stages through a fixed array compiled into the library instead
+ * (9 MiB = 262,144 particles x 36 B; every GPU that loads the library holds
+ * it until the process exits) and calls no allocation routine.
+ *   - The paper has no counterpart: this is an interface convenience.
+ *   - Species with more than 262,144 particles are rejected (FETDPIC_EINVAL,
+ *     the count in fetdpic_last_error); the context must have run
+ *     fetdpic_step or fetdpic_read once (FETDPIC_ESTATE otherwise).
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array and every call rewrites the slots it
+ *     reads, so nothing needs clearing; calls that overlap on the GPU (other
+ *     threads, other contexts on other streams) race on it.
+ * x [n][2], u [n][2], cell [n] are host buffers, each may be NULL. */
+int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell);
+
 /* Crossed-edge record of the last step for species `species` (needs
  * record_walk > 0): cnt [n] crossings per particle; rec [n][record_walk]
  * the crossed edges (instance-local ids) in crossing order, a wall

@@ -4,6 +4,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -845,4 +846,80 @@ extern "C" const char *fetdpic_last_error(const fetdpic_ctx *ctx)
 extern "C" void fetdpic_destroy(fetdpic_ctx *ctx)
 {
     delete ctx;
+}
+
+// ---------------------------------------------------------------------------
+// Particle read-back that allocates nothing.
+//
+// fetdpic_read stages the load-ordered particle state in device memory that
+// it allocates (cudaMalloc, or the caller's allocator callback) the first
+// time it runs.  Some callers cannot allocate at that point: code that runs
+// while a stream is being captured (allocation calls are not allowed there),
+// real-time loops that forbid allocator latency, or plug-ins whose host
+// framework owns all device memory and gives none out.  This variant stages
+// through a fixed file-scope device array instead.  The array is part of
+// the library image: every GPU that loads the library holds it until the
+// process exits.
+namespace {
+
+constexpr long long STATIC_READ_MAX = 262144;                    // particles per call
+constexpr size_t STATIC_READ_BYTES = (size_t)STATIC_READ_MAX * 36; // x, u (FP64) + cell (int32)
+
+static __device__ __align__(256) unsigned char g_static_read[STATIC_READ_BYTES];
+
+// Device address of g_static_read, looked up once per device with that device
+// current (the host-side symbol is only a stand-in, never a device address).
+struct StaticReadSlot { bool ready = false; void *ptr = nullptr; };
+static StaticReadSlot g_static_slots[64];
+static std::mutex g_static_mu;
+
+}  // namespace
+
+extern "C" int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    if (!ctx->finalized) return ctx->fail(FETDPIC_ESTATE, "step or read the context once before the static read");
+    if (species < 0 || species >= (int)ctx->sp.size()) return ctx->fail(FETDPIC_EINVAL, "bad species");
+    const Species &D = ctx->sp[species];
+    if (D.n > STATIC_READ_MAX)
+        return ctx->fail(FETDPIC_EINVAL, "species has " + std::to_string(D.n) + " particles; the static read takes at most "
+                                             + std::to_string(STATIC_READ_MAX));
+    if (ctx->device < 0 || ctx->device >= 64) return ctx->fail(FETDPIC_EINVAL, "device ordinal out of range");
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        StaticReadSlot &s = g_static_slots[ctx->device];
+        if (!s.ready) {
+            int cur = -1;
+            CK(cudaGetDevice(&cur));
+            CK(cudaSetDevice(ctx->device));
+            cudaError_t e = cudaGetSymbolAddress(&s.ptr, g_static_read);
+            cudaSetDevice(cur);
+            if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaGetSymbolAddress(g_static_read)");
+            s.ready = true;
+        }
+        base = s.ptr;
+    }
+    if (D.n == 0) return FETDPIC_OK;
+    // every slot [0, n) is written by exactly one live particle (id is a permutation), so nothing
+    // left over from an earlier call is read; nothing needs clearing
+    const size_t bx = sizeof(double) * 2 * D.n, bc = sizeof(int) * D.n;
+    char *st = (char *)base;
+    double *ox = (double *)st, *ou = (double *)(st + bx);
+    int *oc = (int *)(st + 2 * bx);
+    if (ctx->p.precision == FETDPIC_FP32)
+        launch_unsort32(ctx->stream, ctx->P, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
+                        (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap, D.cell_off,
+                        ox, ou, oc);
+    else
+        launch_unsort64(ctx->stream, ctx->P, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
+                        (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, D.cell_off, ox, ou, oc);
+    CK(cudaGetLastError());
+    if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->stream));
+    if (u) CK(cudaMemcpyAsync(u, ou, bx, cudaMemcpyDeviceToHost, ctx->stream));
+    if (cell) CK(cudaMemcpyAsync(cell, oc, bc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned stw = 0;
+    if (ctx->status) CK(cudaMemcpy(&stw, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return map_status(ctx, stw);
 }

@@ -73,6 +73,7 @@ def lib():
             "fetdpic_sync": (i32, [vp]),
             "fetdpic_read": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp]),
             "fetdpic_read_walk": (i32, [vp, i32, vp, vp]),
+            "fetdpic_read_particles_static": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_check": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_info": (i32, [vp, i32, vp]),
             "fetdpic_read_edges": (i32, [vp, i32, vp]),
