@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--variant", type=int, default=0, help="FP32 particle-kernel variant (0 = library default)")
     return ap.parse_args()
 
 
@@ -199,7 +200,7 @@ def main():
 
     def timed_run(precision, steps, warmup, stages=True):
         sim = fetdpic.Simulation(w, precision=precision, spai_level=2, sort_interval=args.sort_interval,
-                                 time_stages=stages, stream=stream)
+                                 time_stages=stages, stream=stream, kernel_variant=args.variant)
         sim.load()
         sim.step(warmup, args.pusher).sync()
         fetdpic.fetdpic_stage_times(sim.h)            # reset the sums

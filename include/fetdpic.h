@@ -100,6 +100,8 @@ typedef struct {
     int block_size;          /* particle-kernel threads per block; 0 = tuned default */
     int use_graphs;          /* 1 = replay steps from a captured CUDA graph; 0 = plain launches */
     int time_stages;         /* 1 = record CUDA events between stages (fetdpic_stage_times) */
+    int kernel_variant;      /* FP32 particle kernel: minimum resident 256-thread blocks per SM the
+                                register allocation targets, 2, 3 or 4; 0 = tuned default */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);

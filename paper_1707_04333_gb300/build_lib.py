@@ -24,7 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = {
     "kernels_fp64.cu": ["-fmad=false"],
-    "kernels_fp32.cu": [],
+    "kernels_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "kernels_common.cu": [],
     "fetdpic_api.cu": [],
 }

@@ -21,6 +21,7 @@ constexpr double CODATA_EPS0 = 8.8541878128e-12;
 constexpr double CODATA_MU0 = 1.25663706212e-6;
 constexpr double CODATA_C = 299792458.0;
 constexpr long long SPECIES_ALIGN = 1024;   // species storage ranges start on this multiple
+constexpr int FP32_SHIFT = 25;              // fixed-point fraction bits of the FP32-path current
 
 struct StagedSpecies {
     int inst;
@@ -45,7 +46,7 @@ struct fetdpic_ctx {
     long long nfree = 0;
 
     // device: mesh and fields
-    Geo64 *geo64 = nullptr; Geo32 *geo32 = nullptr; Topo *topo = nullptr;
+    Geo64 *geo64 = nullptr; Cst32 *cst32 = nullptr; double2 *dtinv = nullptr; Topo *topo = nullptr;
     Rec64 *rec64 = nullptr; Rec32 *rec32 = nullptr;
     double *e = nullptr, *b = nullptr, *d = nullptr, *r = nullptr, *j = nullptr;
     unsigned long long *ifix = nullptr;
@@ -62,11 +63,13 @@ struct fetdpic_ctx {
     bool finalized = false;
     std::vector<Species> sp;
     Species *sp_dev = nullptr;
+    Sp32 *sp32_dev = nullptr;
     long long P = 0, nblocks = 0;
     int block = 256;
     int *cell = nullptr, *cell_tmp = nullptr, *id = nullptr, *id_tmp = nullptr;
     void *f[4] = {nullptr, nullptr, nullptr, nullptr}, *f_tmp[4] = {nullptr, nullptr, nullptr, nullptr};
     short *blk_sp = nullptr;
+    short *chunk_sp = nullptr;               // species of each 32-particle chunk
     int *hist = nullptr, *hoff = nullptr, *scan_tmp = nullptr; long long hist_n = 0;
     long long *pad_adj = nullptr;
     int *rec_cnt = nullptr, *rec = nullptr;
@@ -196,7 +199,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
 
     // ---- host images of the device tables
     std::vector<Geo64> g64(ctx->F);
-    std::vector<Geo32> g32(P.precision == FETDPIC_FP32 ? ctx->F : 0);
+    std::vector<Cst32> g32(P.precision == FETDPIC_FP32 ? ctx->F : 0);
+    std::vector<double2> dti(P.precision == FETDPIC_FP32 ? ctx->F : 0);
     std::vector<Topo> tp(ctx->F);
     std::vector<double> e0(ctx->E, 0.0), b0(ctx->F, 0.0), d0(ctx->E, 0.0);
     std::vector<int2> efac(ctx->E);
@@ -221,14 +225,6 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             G.dt = I.dt;
             G.hb = 1.0 / (P.mu0 * (0.5 * M.d2A[f]));
             G.pad = 0;
-            if (!g32.empty()) {
-                Geo32 &H = g32[co + f];
-                for (int m = 0; m < 3; ++m) {
-                    H.G[2 * m] = (float)(P.c * I.dt * M.gx[3 * f + m]);
-                    H.G[2 * m + 1] = (float)(P.c * I.dt * M.gy[3 * f + m]);
-                }
-                H.pad[0] = H.pad[1] = 0.f;
-            }
             Topo &T = tp[co + f];
             for (int m = 0; m < 3; ++m) {
                 const int eg = eo + M.tedge[3 * f + m];
@@ -238,6 +234,16 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             }
             T.inst = k;
             b0[co + f] = I.b0 * (0.5 * M.d2A[f]);          // b_f = B0 A_f
+            if (!g32.empty()) {
+                Cst32 &H = g32[co + f];
+                for (int m = 0; m < 3; ++m) {
+                    H.G[2 * m] = (float)(P.c * I.dt * M.gx[3 * f + m]);
+                    H.G[2 * m + 1] = (float)(P.c * I.dt * M.gy[3 * f + m]);
+                    H.nb[m] = T.nb[m];
+                }
+                H.ew0 = T.ew[0]; H.ew1 = T.ew[1]; H.ew2 = T.ew[2];
+                dti[co + f] = make_double2(I.dt, M.inv2A[f]);
+            }
         }
         for (int e = 0; e < M.ne; ++e) {
             const int a = M.edge[2 * e], bnode = M.edge[2 * e + 1];
@@ -268,7 +274,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     try {
         ctx->geo64 = ctx->alloc<Geo64>(ctx->F);
         if (P.precision == FETDPIC_FP32) {
-            ctx->geo32 = ctx->alloc<Geo32>(ctx->F);
+            ctx->cst32 = ctx->alloc<Cst32>(ctx->F);
+            ctx->dtinv = ctx->alloc<double2>(ctx->F);
             ctx->rec32 = ctx->alloc<Rec32>(ctx->F);
         } else {
             ctx->rec64 = ctx->alloc<Rec64>(ctx->F);
@@ -296,7 +303,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     }
     int rc = FETDPIC_OK;
     rc = rc ? rc : upload(ctx, ctx->geo64, g64.data(), g64.size());
-    if (!g32.empty()) rc = rc ? rc : upload(ctx, ctx->geo32, g32.data(), g32.size());
+    if (!g32.empty()) rc = rc ? rc : upload(ctx, ctx->cst32, g32.data(), g32.size());
+    if (!dti.empty()) rc = rc ? rc : upload(ctx, ctx->dtinv, dti.data(), dti.size());
     rc = rc ? rc : upload(ctx, ctx->topo, tp.data(), tp.size());
     rc = rc ? rc : upload(ctx, ctx->e, e0.data(), e0.size());
     rc = rc ? rc : upload(ctx, ctx->b, b0.data(), b0.size());
@@ -372,6 +380,9 @@ static int finalize(fetdpic_ctx *ctx)
         for (double w : wcell[k]) wmax = std::max(wmax, w);
         int sh = 62 - (int)std::ceil(std::log2(16.0 * wmax + 1.0));
         sh = std::max(20, std::min(52, sh));
+        // FP32 path: per-particle contributions are reduced across a warp in 32-bit
+        // integers, |contribution| <= 2^25 keeps a 32-lane sum below 2^31
+        if (P.precision == FETDPIC_FP32) sh = FP32_SHIFT;
         ctx->shift[k] = sh;
         const double qr = qref[k] > 0 ? qref[k] : 1.0;
         ctx->unit_host[k] = (qr / ctx->inst[k].dt) * std::ldexp(1.0, -sh);
@@ -414,7 +425,16 @@ static int finalize(fetdpic_ctx *ctx)
     ctx->hist_n = hist_n;
     const bool f32 = P.precision == FETDPIC_FP32;
     const size_t fb = f32 ? 4 : 8;
+    std::vector<Sp32> s32(std::max(ns, 1));
+    for (int s = 0; s < ns; ++s) {
+        const Species &D = ctx->sp[s];
+        Sp32 &T = s32[s];
+        T.kappa = D.kappa; T.xe_x = D.xe_x; T.xe_y = D.xe_y; T.xb = D.xb;
+        T.wfix = (float)D.wfix;
+        T.inst = D.inst; T.edge_off = ctx->edge_off[D.inst]; T.pad = 0;
+    }
     try {
+        ctx->sp32_dev = ctx->alloc<Sp32>(s32.size());
         ctx->sp_dev = ctx->alloc<Species>(std::max(ns, 1));
         ctx->cell = ctx->alloc<int>(ctx->P);
         ctx->cell_tmp = ctx->alloc<int>(ctx->P);
@@ -425,6 +445,7 @@ static int finalize(fetdpic_ctx *ctx)
             ctx->f_tmp[k] = ctx->alloc<char>(fb * ctx->P);
         }
         ctx->blk_sp = ctx->alloc<short>(std::max<long long>(ctx->nblocks, 1));
+        ctx->chunk_sp = ctx->alloc<short>(std::max<long long>(ctx->P / 32, 1));
         ctx->hist = ctx->alloc<int>(std::max<long long>(hist_n, 1));
         ctx->hoff = ctx->alloc<int>(std::max(ns, 1));
         ctx->scan_tmp = ctx->alloc<int>(scan_tmp_ints(std::max<long long>(hist_n, 1)));
@@ -441,11 +462,13 @@ static int finalize(fetdpic_ctx *ctx)
     std::vector<char> fh[4];
     for (int k = 0; k < 4; ++k) fh[k].assign(fb * ctx->P, 0);
     std::vector<short> blk(ctx->nblocks);
+    std::vector<short> chk(ctx->P / 32);
     for (int s = 0; s < ns; ++s) {
         const StagedSpecies &S = ctx->staged[s];
         const Species &D = ctx->sp[s];
         const HostMesh &M = ctx->mesh[S.inst];
         for (long long b = D.off / ctx->block; b < (D.off + D.cap) / ctx->block; ++b) blk[b] = (short)s;
+        for (long long b = D.off / 32; b < (D.off + D.cap) / 32; ++b) chk[b] = (short)s;
         for (long long k = 0; k < D.n; ++k) {
             const long long q = D.off + k;
             cell[q] = D.cell_off + S.cell[k];
@@ -467,11 +490,13 @@ static int finalize(fetdpic_ctx *ctx)
     }
     int rc = FETDPIC_OK;
     rc = rc ? rc : upload(ctx, ctx->sp_dev, ctx->sp.data(), ctx->sp.size());
+    rc = rc ? rc : upload(ctx, ctx->sp32_dev, s32.data(), s32.size());
     rc = rc ? rc : upload(ctx, ctx->cell, cell.data(), cell.size());
     rc = rc ? rc : upload(ctx, ctx->cell_tmp, cell.data(), cell.size());   // padding stays -1 in both buffers
     rc = rc ? rc : upload(ctx, ctx->id, id.data(), id.size());
     for (int k = 0; k < 4; ++k) rc = rc ? rc : upload(ctx, (char *)ctx->f[k], fh[k].data(), fh[k].size());
     rc = rc ? rc : upload(ctx, ctx->blk_sp, blk.data(), blk.size());
+    rc = rc ? rc : upload(ctx, ctx->chunk_sp, chk.data(), chk.size());
     rc = rc ? rc : upload(ctx, ctx->hoff, hoff.data(), hoff.size());
     rc = rc ? rc : upload(ctx, ctx->pad_adj, pad_adj.data(), pad_adj.size());
     rc = rc ? rc : upload(ctx, ctx->inst_unit, ctx->unit_host.data(), ctx->unit_host.size());
@@ -500,8 +525,9 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
 static StepArgs32 args32(fetdpic_ctx *ctx)
 {
     StepArgs32 a{};
-    a.geo = ctx->geo32; a.topo = ctx->topo; a.rec = ctx->rec32;
-    a.sp = ctx->sp_dev; a.blk_sp = ctx->blk_sp;
+    a.cst = ctx->cst32; a.rec = ctx->rec32;
+    a.sp = ctx->sp32_dev; a.chunk_sp = ctx->chunk_sp; a.nchunks = ctx->P / 32;
+    a.variant = ctx->p.kernel_variant;
     a.l0 = (float *)ctx->f[0]; a.l1 = (float *)ctx->f[1]; a.ux = (float *)ctx->f[2]; a.uy = (float *)ctx->f[3];
     a.cell = ctx->cell;
     a.ifix = ctx->ifix; a.status = ctx->status;
@@ -563,7 +589,8 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     long long launches = 0;
     const bool f32 = ctx->p.precision == FETDPIC_FP32;
     if (timed) mark(ctx, -1);
-    if (f32) launch_faraday32(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec32, ctx->p.c);
+    if (f32) launch_faraday32(ctx->stream, ctx->F, ctx->cst32, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
+                              (float)(0.5 / (ctx->p.c * ctx->p.c)));
     else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
     launches += ctx->F > 0;
     if (timed) mark(ctx, 0);

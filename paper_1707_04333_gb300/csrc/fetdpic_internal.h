@@ -56,10 +56,23 @@ struct __align__(16) Geo64 {
 };
 static_assert(sizeof(Geo64) == 128, "Geo64 layout");
 
-// FP32 geometry: G_m = c dt grad lambda_m (dimensionless step in barycentrics per unit v/c).
-struct __align__(16) Geo32 {
+// FP32 per-triangle constants (48 B): G_m = c dt grad lambda_m (barycentric
+// step per unit v/c), edge words 1 and 2 (word 0 rides in the field record so
+// the main path reads 32 + 32 B), neighbour words (walk only), as in Topo.
+struct __align__(16) Cst32 {
     float G[6];                             // (G0x, G0y, G1x, G1y, G2x, G2y)
-    float pad[2];
+    int ew1, ew2;
+    int nb[3];
+    int ew0;                                // copied into Rec32 by the Faraday kernel
+};
+static_assert(sizeof(Cst32) == 48, "Cst32 layout");
+
+// FP32-path species parameters, read with uniform loads (32 B).
+struct __align__(16) Sp32 {
+    float kappa;                            // q/m
+    float xe_x, xe_y, xb;                   // external fields pre-scaled (alpha E/c, alpha B)
+    float wfix;                             // (q / q_ref) * 2^shift32
+    int inst, edge_off, pad;
 };
 
 // Topology: edge word = (global edge << 1) | (sign < 0); neighbour word =
@@ -76,7 +89,7 @@ static_assert(sizeof(Topo) == 48, "Topo layout");
 // Faraday kernel): FP64 path: (s_m e_m for m = 0..2, B_z^n); FP32 path:
 // E(lambda) = sum_n lambda_n V_n scaled by dt/(2c), B_z scaled by dt/2.
 struct __align__(32) Rec64 { double se[3]; double bz; };
-struct __align__(32) Rec32 { float v[6]; float bz; float pad; };
+struct __align__(32) Rec32 { float v[6]; float bz; int ew0; };
 
 struct Species {
     double alpha;                           // q dt / (2 m)
@@ -113,8 +126,10 @@ struct StepArgs64 {
 };
 
 struct StepArgs32 {
-    const Geo32 *geo; const Topo *topo; const Rec32 *rec;
-    const Species *sp; const short *blk_sp;
+    const Cst32 *cst; const Rec32 *rec;
+    const Sp32 *sp; const short *chunk_sp;  // species of each 32-particle chunk
+    long long nchunks;
+    int variant;                            // particle-kernel variant (min resident blocks per SM)
     float *l0, *l1, *ux, *uy; int *cell;
     unsigned long long *ifix;
     unsigned *status;
@@ -126,8 +141,8 @@ struct StepArgs32 {
 
 void launch_faraday64(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
                       double *b, Rec64 *rec);
-void launch_faraday32(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
-                      double *b, Rec32 *rec, double c);
+void launch_faraday32(cudaStream_t st, int F, const Cst32 *cst, const double2 *dtinv, const double *e,
+                      double *b, Rec32 *rec, float inv2c2);
 void launch_particles64(cudaStream_t st, int pusher, const StepArgs64 &a);
 void launch_particles32(cudaStream_t st, int pusher, const StepArgs32 &a);
 

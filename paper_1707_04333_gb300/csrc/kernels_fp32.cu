@@ -3,6 +3,12 @@
 // Gather, push, walk and deposit run in FP32; particles with gamma > 10 take
 // the FP64 push (Lorentz factor and momentum update), where FP32 loses the
 // 1 - v/c and sigma cancellations.  The field update stays FP64.
+//
+// Built with approximate FP32 division and square root (-prec-div=false
+// -prec-sqrt=false, about 2 ulp): the FP32 path is compared with the FP64
+// oracle at FP32 round-off tolerances, not bit for bit.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "fetdpic_internal.h"
@@ -11,336 +17,469 @@ namespace fetdpic {
 
 // Faraday update in FP64 (in place) and the FP32 field record: in a triangle
 // E(lambda) = sum_m s_m e_m (l_a grad l_b - l_b grad l_a) = sum_n l_n V_n with
-// V_n = s_{n-1} e_{n-1} grad l_{n+1} - s_{n+1} e_{n+1} grad l_{n-1}; stored
-// scaled by dt/(2c) so that q/m times it is alpha E / c.  B_z^n scaled by dt/2.
-__global__ void k_faraday32(int F, const Geo64 *__restrict__ geo, const Topo *__restrict__ topo,
-                            const double *__restrict__ e, double *__restrict__ b, Rec32 *__restrict__ rec,
-                            double c)
+// V_n = s_{n-1} e_{n-1} grad l_{n+1} - s_{n+1} e_{n+1} grad l_{n-1}.  Stored
+// as dt/(2c) V_n = (s_{n-1} e_{n-1} G_{n+1} - s_{n+1} e_{n+1} G_{n-1}) / (2c^2)
+// (G = c dt grad l), so that q/m times it is alpha E / c; B_z^n stored as
+// (dt/2) B_z = (dt/2) (b^{n+1/2} + b^{n-1/2}) / (2A).
+__global__ void __launch_bounds__(256) k_faraday32(int F, const Cst32 *__restrict__ cst,
+                                                   const double2 *__restrict__ dtinv,
+                                                   const double *__restrict__ e, double *__restrict__ b,
+                                                   Rec32 *__restrict__ rec, float inv2c2)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
-    const Topo t = topo[f];
-    const Geo64 &G = geo[f];
+    const float4 *cp = reinterpret_cast<const float4 *>(cst + f);
+    const float4 c0 = cp[0], c1 = cp[1], c2 = cp[2];
+    const float G[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
+    const int ew[3] = {__float_as_int(c2.w), __float_as_int(c1.z), __float_as_int(c1.w)};
     double se[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const double v = e[t.ew[m] >> 1];
-        se[m] = (t.ew[m] & 1) ? -v : v;
+        const double v = e[ew[m] >> 1];
+        se[m] = (ew[m] & 1) ? -v : v;
     }
+    const double2 di = dtinv[f];                    // (dt, 1/(2A))
     const double bo = b[f];
-    const double bn = bo - G.dt * ((se[0] + se[1]) + se[2]);
+    const double bn = bo - di.x * ((se[0] + se[1]) + se[2]);
     b[f] = bn;
-    const double s = G.dt / (2.0 * c);
+    float s[3] = {(float)se[0] * inv2c2, (float)se[1] * inv2c2, (float)se[2] * inv2c2};
     Rec32 r;
 #pragma unroll
     for (int n = 0; n < 3; ++n) {
         const int nm = (n + 2) % 3, np = (n + 1) % 3;
-        r.v[2 * n] = (float)(s * (se[nm] * G.gx[np] - se[np] * G.gx[nm]));
-        r.v[2 * n + 1] = (float)(s * (se[nm] * G.gy[np] - se[np] * G.gy[nm]));
+        r.v[2 * n] = s[nm] * G[2 * np] - s[np] * G[2 * nm];
+        r.v[2 * n + 1] = s[nm] * G[2 * np + 1] - s[np] * G[2 * nm + 1];
     }
-    r.bz = (float)(0.5 * G.dt * ((bn + bo) * G.inv2A));
-    r.pad = 0.f;
-    rec[f] = r;
+    r.bz = (float)(0.5 * di.x * ((bn + bo) * di.y));
+    float4 *rp = reinterpret_cast<float4 *>(rec + f);
+    rp[0] = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+    rp[1] = make_float4(r.v[4], r.v[5], r.bz, __int_as_float(ew[0]));
 }
 
-void launch_faraday32(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
-                      double *b, Rec32 *rec, double c)
+void launch_faraday32(cudaStream_t st, int F, const Cst32 *cst, const double2 *dtinv, const double *e,
+                      double *b, Rec32 *rec, float inv2c2)
 {
     if (F <= 0) return;
-    k_faraday32<<<(F + 255) / 256, 256, 0, st>>>(F, geo, topo, e, b, rec, c);
+    k_faraday32<<<(F + 255) / 256, 256, 0, st>>>(F, cst, dtinv, e, b, rec, inv2c2);
 }
 
 // --------------------------------------------------------------- pushers
 // Dimensionless (c = 1): eps = alpha E / c, beta = alpha B, u in units of c.
+// Returns 1/gamma^{n+1/2} (the position update needs v = u/gamma).
+
+template <typename T> __device__ __forceinline__ T rsqrt_(T x);
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <typename T> __device__ __forceinline__ T rcp_(T x);
+template <> __device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
 
 template <int PUSHER, typename T>
-__device__ __forceinline__ void push_c1(T &ux, T &uy, T &g, T ex, T ey, T bz)
+__device__ __forceinline__ T push_c1(T &ux, T &uy, T ex, T ey, T bz)
 {
     const T one = T(1), half = T(0.5), two = T(2), four = T(4);
     const T bb = bz * bz;
     if (PUSHER == FETDPIC_VAY) {
-        const T g0 = sqrt(one + ux * ux + uy * uy);
-        const T vx = ux / g0, vy = uy / g0;
+        // Sec. II.C(b): u' = u + 2 eps + v x beta; gamma^{n+1/2} from the quartic root
+        // sqrt((sigma + sqrt(sigma^2 + 4|beta|^2))/2); t = beta/gamma; s = 1/(1+t^2)
+        const T ig0 = rsqrt_(one + ux * ux + uy * uy);
+        const T vx = ux * ig0, vy = uy * ig0;
         const T upx = ux + two * ex + vy * bz;
         const T upy = uy + two * ey - vx * bz;
-        const T gp2 = one + upx * upx + upy * upy;
-        const T sigma = gp2 - bb;
-        const T gn = sqrt(half * (sigma + sqrt(sigma * sigma + four * bb)));
-        const T tz = bz / gn;
-        const T s = one / (one + tz * tz);
+        const T sigma = one + upx * upx + upy * upy - bb;
+        const T r2 = sigma * sigma + four * bb;            // > 0: sigma >= 1 - |beta|^2 + |u'|^2 ...
+        const T root = r2 * rsqrt_(r2);
+        const T ign = rsqrt_(half * (sigma + root));        // 1/gamma^{n+1/2}
+        const T tz = bz * ign;
+        const T s = rcp_(one + tz * tz);
         ux = s * (upx + upy * tz);
         uy = s * (upy - upx * tz);
-        g = gn;
-        return;
+        return ign;
     }
+    // Boris family, Eqs. (Boris.u1-u4)
     const T umx = ux + ex, umy = uy + ey;
-    const T gbar = sqrt(one + umx * umx + umy * umy);
+    const T g2 = one + umx * umx + umy * umy;
     T tz;
     if (PUSHER == FETDPIC_HC) {
-        const T sigma = gbar * gbar - bb;
-        const T gh = sqrt(half * (sigma + sqrt(sigma * sigma + four * bb)));
-        tz = bz / gh;
+        // Sec. II.C(c): t = beta / gamma_H, gamma_H^2 = (sigma + sqrt(sigma^2 + 4|beta|^2))/2
+        const T sigma = g2 - bb;
+        const T r2 = sigma * sigma + four * bb;
+        const T root = r2 * rsqrt_(r2);
+        tz = bz * rsqrt_(half * (sigma + root));
     } else if (PUSHER == FETDPIC_BORIS_TAN) {
+        const T igbar = rsqrt_(g2);
         const T nb = abs(bz);
-        tz = (nb == T(0)) ? T(0) : (bz / nb) * tan(nb / gbar);
+        tz = (nb == T(0)) ? T(0) : (bz / nb) * tan(nb * igbar);
     } else {
-        tz = bz / gbar;
+        tz = bz * rsqrt_(g2);
     }
-    const T sz = (two * tz) / (one + tz * tz);
+    const T sz = (two * tz) * rcp_(one + tz * tz);
     const T uprx = umx + umy * tz, upry = umy - umx * tz;
     ux = (umx + upry * sz) + ex;
     uy = (umy - uprx * sz) + ey;
-    g = sqrt(one + ux * ux + uy * uy);
+    return rsqrt_(one + ux * ux + uy * uy);
 }
 
-__device__ __forceinline__ void seg_current32(const float *ls, const float *lf, float w, long long *v)
+// FP64 push for gamma > 10 (rare; kept out of line so its registers do not
+// count against the FP32 main path).  Arguments and result by value, so no
+// caller variable needs an address.  Returns (u_x, u_y, v_x, v_y) in units of
+// c and 1/gamma.
+struct PushOut { float ux, uy, vx, vy, ig; };
+
+template <int PUSHER>
+__device__ __noinline__ PushOut push_fp64(float ux, float uy, float ex, float ey, float bz)
+{
+    double dux = ux, duy = uy;
+    const double dig = push_c1<PUSHER, double>(dux, duy, (double)ex, (double)ey, (double)bz);
+    PushOut o;
+    o.ux = (float)dux; o.uy = (float)duy;
+    o.vx = (float)(dux * dig); o.vy = (float)(duy * dig);
+    o.ig = (float)dig;
+    return o;
+}
+
+// Fixed-point current of one sub-segment, Eq. (I.assign): round(w (l_a^s l_b^f
+// - l_a^f l_b^s)) per local edge m = (a, b) = (m+1, m+2); |.| <= 2^shift32, so a
+// sum over one warp fits in 32 bits.
+__device__ __forceinline__ void seg_current32(const float *ls, const float *lf, float w, int *v)
 {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         const int a = (m + 1) % 3, b = (m + 2) % 3;
         const float d = ls[a] * lf[b] - lf[a] * ls[b];
-        v[m] = __float2ll_rn(d * w);
+        v[m] = __float2int_rn(d * w);
     }
 }
 
-__device__ __forceinline__ void add_seg32(unsigned long long *ifix, const Topo &t, const long long *v)
+__device__ __forceinline__ void add_seg32(unsigned long long *ifix, const int *ew, const int *v)
 {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const long long s = (t.ew[m] & 1) ? -v[m] : v[m];
-        if (s != 0) atomicAdd(ifix + (t.ew[m] >> 1), (unsigned long long)s);
+        const long long s = (ew[m] & 1) ? -(long long)v[m] : (long long)v[m];
+        if (s != 0) atomicAdd(ifix + (ew[m] >> 1), (unsigned long long)s);
     }
 }
 
-// Walk step in barycentrics.  The path is r(tau) = r^n + tau * c dt v/c,
-// tau in [0, 1]; inside triangle f, l_k(tau) = lin_k + (tau - tin) g_k with
-// g_k = G_k . v.  Exit through the edge whose coordinate first reaches 0
-// (lowest local index on ties), excluding the entry edge.
+// Exit edge of the path inside the current triangle: l_k(tau) = lin_k +
+// (tau - tin) g_k for tau in [tin, 1].  Candidates are edges k != entry with
+// l_k(1) < 0; the exit is the smallest tau_k = tin + lin_k/(-g_k) (lowest k on
+// ties), compared by cross-multiplication so only the chosen edge divides.
 __device__ __forceinline__ int exit_edge(const float *lin, const float *g, float tin, int min, float &tb)
 {
-    int best = -1;
-    tb = 2.f;
     const float rem = 1.f - tin;
+    int best = -1;
+    float bn = 0.f, bd = 1.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (k == min) continue;
-        const float lf = lin[k] + rem * g[k];
-        if (lf < 0.f) {
-            float t = (g[k] < 0.f) ? tin + lin[k] / (-g[k]) : tin;
-            t = fminf(fmaxf(t, tin), 1.f);
-            if (best < 0 || t < tb) { best = k; tb = t; }
+        if (lin[k] + rem * g[k] < 0.f) {
+            float num = fmaxf(lin[k], 0.f), den = -g[k];
+            if (!(den > 0.f)) { num = 0.f; den = 1.f; }
+            if (best < 0 || num * bd < bn * den) { best = k; bn = num; bd = den; }
         }
     }
+    tb = best < 0 ? 1.f : fminf(tin + bn / bd, 1.f);
     return best;
 }
 
-template <int PUSHER>
-__global__ void __launch_bounds__(256) k_particles32(StepArgs32 a)
+// Register-resident element k (0..2) of a 3-array (no dynamic indexing, so no local memory).
+template <typename T>
+__device__ __forceinline__ T sel3(const T *a, int k)
 {
-    __shared__ Species S;
-    const long long blk = blockIdx.x;
-    if (threadIdx.x == 0) S = a.sp[a.blk_sp[blk]];
-    __syncthreads();
-    const long long p = blk * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    int f = a.cell[p];
-    const bool live = f >= 0;
+    return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]);
+}
 
-    long long v0[3] = {0, 0, 0};
-    Topo t0;
-    int key = -1;
-    bool walking = false;
-    float lin[3] = {0.f, 0.f, 0.f}, g[3] = {0.f, 0.f, 0.f};
-    float vx = 0.f, vy = 0.f, ux = 0.f, uy = 0.f, gam = 1.f, tin = 0.f;
-    float lfin[3] = {0.f, 0.f, 0.f};
-    int min = -1, ncross = 0;
-    Topo tc;
+// Walk state of a particle whose path leaves its triangle, queued per warp.
+struct WalkItem {
+    long long p;                 // particle index
+    int f;                       // starting triangle
+    int sp;                      // species
+    float l0, l1, l2, pad, ux, uy, vx, vy;
+};
+static_assert(sizeof(WalkItem) == 48, "WalkItem layout");
 
-    if (live) {
-        tc = a.topo[f];
-        const float4 *rp = reinterpret_cast<const float4 *>(a.rec + f);
-        const float4 r0 = rp[0], r1 = rp[1];
-        const float4 *gp = reinterpret_cast<const float4 *>(a.geo + f);
-        const float4 q0 = gp[0], q1 = gp[1];
-        const float G[6] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y};
-        const float l0 = a.l0[p], l1 = a.l1[p];
-        const float l2 = 1.f - l0 - l1;
-        ux = a.ux[p]; uy = a.uy[p];
-        // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
-        const float ex = S.kappa * (l0 * r0.x + l1 * r0.z + l2 * r1.x) + S.xe_x;
-        const float ey = S.kappa * (l0 * r0.y + l1 * r0.w + l2 * r1.y) + S.xe_y;
-        const float bz = S.kappa * r1.z + S.xb;
-        // push (Sec. II.C); FP64 when gamma > 10
-        const float gin2 = 1.f + ux * ux + uy * uy;
-        if (gin2 > 100.f) {
-            double dux = ux, duy = uy, dg;
-            push_c1<PUSHER, double>(dux, duy, dg, (double)ex, (double)ey, (double)bz);
-            ux = (float)dux; uy = (float)duy;
-            vx = (float)(dux / dg); vy = (float)(duy / dg);
-            gam = (float)dg;
-        } else {
-            push_c1<PUSHER, float>(ux, uy, gam, ex, ey, bz);
-            vx = ux / gam; vy = uy / gam;
-        }
-        if (!isfinite(gam) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
-        // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
+__device__ __forceinline__ void load_cst(const Cst32 *cst, int f, float *G, int *ew, int *nb)
+{
+    const float4 *cp = reinterpret_cast<const float4 *>(cst + f);
+    const float4 c0 = cp[0], c1 = cp[1], c2 = cp[2];
+    G[0] = c0.x; G[1] = c0.y; G[2] = c0.z; G[3] = c0.w; G[4] = c1.x; G[5] = c1.y;
+    ew[0] = __float_as_int(c2.w); ew[1] = __float_as_int(c1.z); ew[2] = __float_as_int(c1.w);
+    nb[0] = __float_as_int(c2.x); nb[1] = __float_as_int(c2.y); nb[2] = __float_as_int(c2.z);
+}
+
+// Walk one queued particle along r(tau) = r^n + tau c dt v/c, tau in [0, 1],
+// through the triangles it crosses (the current splits the path per triangle,
+// Eq. (I.assign)): exit test, deposit of each sub-segment with direct integer
+// atomics, hand-off to the neighbour or specular reflection at a PEC wall, and
+// the final particle state.
+__device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkItem it)
+{
+    const Sp32 *spp = a.sp + it.sp;
+    const float wfix = __ldg(&spp->wfix);
+    const int edge_off = __ldg(&spp->edge_off);
+    const long long p = it.p;
+    int f = it.f, ncross = 0, min = -1;
+    float lin[3] = {it.l0, it.l1, it.l2};
+    float tin = 0.f, ux = it.ux, uy = it.uy, vx = it.vx, vy = it.vy;
+    float lfin[3];
+    float G[6];
+    int ew[3], nb[3];
+    load_cst(a.cst, f, G, ew, nb);
+    for (;;) {
+        float g[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) g[k] = G[2 * k] * vx + G[2 * k + 1] * vy;
-        lin[0] = l0; lin[1] = l1; lin[2] = l2;
-        float tb;
-        const int best = exit_edge(lin, g, 0.f, -1, tb);
-        t0 = tc;
-        key = f;
-        if (best < 0) {
-            lfin[0] = lin[0] + g[0];
-            lfin[1] = lin[1] + g[1];
-            lfin[2] = 1.f - lfin[0] - lfin[1];
-            seg_current32(lin, lfin, S.wfix32, v0);
-        } else {
-            float lout[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) lout[k] = lin[k] + tb * g[k];
-            lout[best] = 0.f;
-            seg_current32(lin, lout, S.wfix32, v0);
-            walking = true;
-            const int eg = tc.ew[best] >> 1;
-            if (ncross >= a.max_cross) {
-                lfin[0] = lout[0]; lfin[1] = lout[1]; lfin[2] = lout[2];
-                atomicOr(a.status, (unsigned)ST_WALK);
-                walking = false;
-            } else {
-                const int nbw = tc.nb[best];
-                if (a.rec_cap > ncross) a.wrec[p * a.rec_cap + ncross] = nbw < 0 ? -(eg - a.edge_off[S.inst] + 1) : eg - a.edge_off[S.inst];
-                ++ncross;
-                if (nbw < 0) {
-                    // specular reflection about the wall: normal along G_best
-                    const float gxb = G[2 * best], gyb = G[2 * best + 1];
-                    const float gg = gxb * gxb + gyb * gyb;
-                    const float pu = (ux * gxb + uy * gyb) / gg;
-                    ux -= 2.f * pu * gxb; uy -= 2.f * pu * gyb;
-                    const float pv = (vx * gxb + vy * gyb) / gg;
-                    vx -= 2.f * pv * gxb; vy -= 2.f * pv * gyb;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) g[k] = G[2 * k] * vx + G[2 * k + 1] * vy;
-                    min = best;
-                    lin[0] = lout[0]; lin[1] = lout[1]; lin[2] = lout[2];
-                } else {
-                    const int m2 = nbw & 3;
-                    float l2n[3];
-                    l2n[m2] = 0.f;
-                    l2n[(m2 + 1) % 3] = lout[(best + 2) % 3];
-                    l2n[(m2 + 2) % 3] = lout[(best + 1) % 3];
-                    lin[0] = l2n[0]; lin[1] = l2n[1]; lin[2] = l2n[2];
-                    f = nbw >> 2;
-                    min = m2;
-                    tc = a.topo[f];
-                    const float4 *gq = reinterpret_cast<const float4 *>(a.geo + f);
-                    const float4 w0 = gq[0], w1 = gq[1];
-                    g[0] = w0.x * vx + w0.y * vy;
-                    g[1] = w0.z * vx + w0.w * vy;
-                    g[2] = w1.x * vx + w1.y * vy;
-                }
-                tin = tb;
-            }
-        }
-    }
-
-    {
-        const unsigned full = 0xffffffffu;
-        const int kn = __shfl_down_sync(full, key, 1);
-        const bool tail = (lane == 31) || (kn != key);
-        const unsigned tails = __ballot_sync(full, tail);
-        const int seg_end = lane + __ffs(tails >> lane) - 1;
-        const int kp = __shfl_up_sync(full, key, 1);
-        const bool head = (lane == 0) || (kp != key);
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const long long o = __shfl_down_sync(full, v0[m], off);
-                if (lane + off <= seg_end) v0[m] += o;
-            }
-        }
-        if (head && key >= 0) add_seg32(a.ifix, t0, v0);
-    }
-
-    while (walking) {
         float tb;
         const int best = exit_edge(lin, g, tin, min, tb);
-        long long v[3];
+        int v[3];
         if (best < 0) {
             const float rem = 1.f - tin;
             lfin[0] = lin[0] + rem * g[0];
             lfin[1] = lin[1] + rem * g[1];
             lfin[2] = 1.f - lfin[0] - lfin[1];
-            seg_current32(lin, lfin, S.wfix32, v);
-            add_seg32(a.ifix, tc, v);
+            seg_current32(lin, lfin, wfix, v);
+            add_seg32(a.ifix, ew, v);
             break;
         }
         float lout[3];
         const float dtau = tb - tin;
-        for (int k = 0; k < 3; ++k) lout[k] = lin[k] + dtau * g[k];
-        lout[best] = 0.f;
-        seg_current32(lin, lout, S.wfix32, v);
-        add_seg32(a.ifix, tc, v);
-        const int eg = tc.ew[best] >> 1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lout[k] = (k == best) ? 0.f : lin[k] + dtau * g[k];
+        seg_current32(lin, lout, wfix, v);
+        add_seg32(a.ifix, ew, v);
+        lin[0] = lout[0]; lin[1] = lout[1]; lin[2] = lout[2];
+        tin = tb;
+        const int eg = sel3(ew, best) >> 1;
         if (ncross >= a.max_cross) {
-            lfin[0] = lout[0]; lfin[1] = lout[1]; lfin[2] = lout[2];
+            lfin[0] = lin[0]; lfin[1] = lin[1]; lfin[2] = lin[2];
             atomicOr(a.status, (unsigned)ST_WALK);
             break;
         }
-        const int nbw = tc.nb[best];
-        if (a.rec_cap > ncross) a.wrec[p * a.rec_cap + ncross] = nbw < 0 ? -(eg - a.edge_off[S.inst] + 1) : eg - a.edge_off[S.inst];
+        const int nbw = sel3(nb, best);
+        if (a.rec_cap > ncross) a.wrec[p * a.rec_cap + ncross] = nbw < 0 ? -(eg - edge_off + 1) : eg - edge_off;
         ++ncross;
-        const float4 *gq = reinterpret_cast<const float4 *>(a.geo + f);
         if (nbw < 0) {
-            const float4 w0 = gq[0], w1 = gq[1];
-            const float G[6] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y};
-            const float gxb = G[2 * best], gyb = G[2 * best + 1];
-            const float gg = gxb * gxb + gyb * gyb;
-            const float pu = (ux * gxb + uy * gyb) / gg;
+            // PEC wall: specular reflection of u and of the rest of the path, normal along G_best
+            const float gxs[3] = {G[0], G[2], G[4]}, gys[3] = {G[1], G[3], G[5]};
+            const float gxb = sel3(gxs, best), gyb = sel3(gys, best);
+            const float igg = 1.f / (gxb * gxb + gyb * gyb);
+            const float pu = (ux * gxb + uy * gyb) * igg;
             ux -= 2.f * pu * gxb; uy -= 2.f * pu * gyb;
-            const float pv = (vx * gxb + vy * gyb) / gg;
+            const float pv = (vx * gxb + vy * gyb) * igg;
             vx -= 2.f * pv * gxb; vy -= 2.f * pv * gyb;
-            for (int k = 0; k < 3; ++k) g[k] = G[2 * k] * vx + G[2 * k + 1] * vy;
             min = best;
-            lin[0] = lout[0]; lin[1] = lout[1]; lin[2] = lout[2];
         } else {
+            // hand-off: the neighbour's node m2+1 is our node best+2, its m2+2 our best+1
             const int m2 = nbw & 3;
-            float l2n[3];
-            l2n[m2] = 0.f;
-            l2n[(m2 + 1) % 3] = lout[(best + 2) % 3];
-            l2n[(m2 + 2) % 3] = lout[(best + 1) % 3];
-            lin[0] = l2n[0]; lin[1] = l2n[1]; lin[2] = l2n[2];
+            const float la = sel3(lin, best == 0 ? 2 : best - 1);
+            const float lb = sel3(lin, best == 2 ? 0 : best + 1);
+            lin[0] = m2 == 0 ? 0.f : (m2 == 2 ? la : lb);
+            lin[1] = m2 == 1 ? 0.f : (m2 == 0 ? la : lb);
+            lin[2] = m2 == 2 ? 0.f : (m2 == 1 ? la : lb);
             f = nbw >> 2;
             min = m2;
-            tc = a.topo[f];
-            const float4 *gn = reinterpret_cast<const float4 *>(a.geo + f);
-            const float4 w0 = gn[0], w1 = gn[1];
-            g[0] = w0.x * vx + w0.y * vy;
-            g[1] = w0.z * vx + w0.w * vy;
-            g[2] = w1.x * vx + w1.y * vy;
+            load_cst(a.cst, f, G, ew, nb);
         }
-        tin = tb;
     }
+    a.l0[p] = lfin[0]; a.l1[p] = lfin[1];
+    a.ux[p] = ux; a.uy[p] = uy;
+    a.cell[p] = f;
+    if (a.rec_cap > 0) a.rec_cnt[p] = ncross;
+}
 
-    if (live) {
-        a.l0[p] = lfin[0]; a.l1[p] = lfin[1];
-        a.ux[p] = ux; a.uy[p] = uy;
-        a.cell[p] = f;
-        if (a.rec_cap > 0) a.rec_cnt[p] = ncross;
+constexpr int P32_BLOCK = 256;
+constexpr int P32_WARPS = P32_BLOCK / 32;
+constexpr int P32_QUEUE = 64;                // walker ring per warp
+
+// Persistent kernel: each warp takes a contiguous range of 32-particle chunks,
+// with the next chunk's particle state loaded into registers while the
+// current one is processed.  Species ranges are padded to 1024, so a chunk
+// never straddles species.  Loads per particle: 20 B of state (coalesced), the
+// triangle constants (64 B) and field record (32 B), shared by the sorted
+// particles of one triangle.  The first sub-segment's current is reduced in
+// 32-bit fixed point over runs of equal triangle across the warp (segmented
+// shuffle scan); the run head widens to 64 bits and adds three integers with
+// atomics.  Particles whose path leaves their triangle (about one in ten) go
+// to the warp's ring in shared memory and are walked 32 at a time, so the
+// divergent walk runs with full warps and the common path only tests that the
+// end point is inside.  Integer sums are exact: the result
+// does not depend on particle, queue or atomic order.
+template <int PUSHER, int MINB>
+__global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
+{
+    __shared__ WalkItem qbuf[P32_WARPS][P32_QUEUE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkItem *q = qbuf[warp];
+    unsigned qhead = 0, qtail = 0;                    // warp-uniform ring positions
+    // warp w takes the contiguous chunks [w K, (w+1) K): consecutive chunks of
+    // sorted particles share triangles, so their records come from L1
+    const long long nwarps = (long long)gridDim.x * P32_WARPS;
+    const long long wid = (long long)blockIdx.x * P32_WARPS + warp;
+    const long long K = (a.nchunks + nwarps - 1) / nwarps;
+    long long c = wid * K;
+    const long long cend = min(c + K, a.nchunks);
+    const unsigned full = 0xffffffffu;
+
+    int fn = -1;
+    float l0n = 0.f, l1n = 0.f, uxn = 0.f, uyn = 0.f;
+    if (c < cend) {
+        const long long pn = c * 32 + lane;
+        fn = a.cell[pn]; l0n = a.l0[pn]; l1n = a.l1[pn]; uxn = a.ux[pn]; uyn = a.uy[pn];
+    }
+    for (; c < cend; ++c) {
+        const long long p = c * 32 + lane;
+        const int f = fn;
+        const float l0 = l0n, l1 = l1n;
+        float ux = uxn, uy = uyn;
+        const long long cn = c + 1;
+        if (cn < cend) {
+            const long long pn = cn * 32 + lane;
+            fn = a.cell[pn]; l0n = a.l0[pn]; l1n = a.l1[pn]; uxn = a.ux[pn]; uyn = a.uy[pn];
+        }
+        const int spid = a.chunk_sp[c];
+        const Sp32 *spp = a.sp + spid;
+        const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
+        const float wfix = __ldg(&spp->wfix);
+        const bool live = f >= 0;
+
+        int v0[3] = {0, 0, 0};
+        int ew0[3] = {0, 0, 0};
+        int key = -1;
+        bool walking = false;
+        float lfin[3] = {0.f, 0.f, 0.f};
+        WalkItem it;
+        if (live) {
+            const float4 *cp = reinterpret_cast<const float4 *>(a.cst + f);
+            const float4 c0 = cp[0], c1 = cp[1];
+            const float4 *rp = reinterpret_cast<const float4 *>(a.rec + f);
+            const float4 r0 = rp[0], r1 = rp[1];
+            ew0[0] = __float_as_int(r1.w); ew0[1] = __float_as_int(c1.z); ew0[2] = __float_as_int(c1.w);
+            const float l2 = 1.f - l0 - l1;
+            // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
+            const float ex = s0.x * (l0 * r0.x + l1 * r0.z + l2 * r1.x) + s0.y;
+            const float ey = s0.x * (l0 * r0.y + l1 * r0.w + l2 * r1.y) + s0.z;
+            const float bz = s0.x * r1.z + s0.w;
+            // push (Sec. II.C); FP64 when gamma > 10
+            float ig, vx, vy;
+            if (1.f + ux * ux + uy * uy > 100.f) {
+                const PushOut o = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
+                ux = o.ux; uy = o.uy; vx = o.vx; vy = o.vy; ig = o.ig;
+            } else {
+                ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
+                vx = ux * ig; vy = uy * ig;
+            }
+            if (!isfinite(ux + uy + ig)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+            // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
+            const float g0 = c0.x * vx + c0.y * vy;
+            const float g1 = c0.z * vx + c0.w * vy;
+            const float g2 = c1.x * vx + c1.y * vy;
+            lfin[0] = l0 + g0;
+            lfin[1] = l1 + g1;
+            lfin[2] = l2 + g2;
+            if (lfin[0] >= 0.f && lfin[1] >= 0.f && lfin[2] >= 0.f) {
+                // stays in its triangle: i_ab += (Q/dt)(l_a^s dl_b - dl_a l_b^s), Eq. (I.assign)
+                // with l^f = l^s + dl
+                key = f;
+                lfin[2] = 1.f - lfin[0] - lfin[1];
+                v0[0] = __float2int_rn((l1 * g2 - g1 * l2) * wfix);
+                v0[1] = __float2int_rn((l2 * g0 - g2 * l0) * wfix);
+                v0[2] = __float2int_rn((l0 * g1 - g0 * l1) * wfix);
+            } else {
+                walking = true;
+                it.p = p; it.f = f; it.sp = spid;
+                it.l0 = l0; it.l1 = l1; it.l2 = l2; it.pad = 0.f;
+                it.ux = ux; it.uy = uy; it.vx = vx; it.vy = vy;
+            }
+        }
+        // queue the walkers of this chunk
+        const unsigned wm = __ballot_sync(full, walking);
+        if (walking) {
+            const unsigned rank = __popc(wm & ((1u << lane) - 1u));
+            q[(qtail + rank) & (P32_QUEUE - 1)] = it;
+        }
+        qtail += __popc(wm);
+
+        // warp segmented reduction of the first sub-segment over runs of equal triangle
+        {
+            const int kn = __shfl_down_sync(full, key, 1);
+            const bool tail = (lane == 31) || (kn != key);
+            const unsigned tails = __ballot_sync(full, tail);
+            const int seg_end = lane + __ffs(tails >> lane) - 1;
+            const int kp = __shfl_up_sync(full, key, 1);
+            const bool head = (lane == 0) || (kp != key);
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int o0 = __shfl_down_sync(full, v0[0], off);
+                const int o1 = __shfl_down_sync(full, v0[1], off);
+                const int o2 = __shfl_down_sync(full, v0[2], off);
+                if (lane + off <= seg_end) { v0[0] += o0; v0[1] += o1; v0[2] += o2; }
+            }
+            if (head && key >= 0) add_seg32(a.ifix, ew0, v0);
+        }
+        if (live && !walking) {
+            a.l0[p] = lfin[0]; a.l1[p] = lfin[1];
+            a.ux[p] = ux; a.uy[p] = uy;
+            if (a.rec_cap > 0) a.rec_cnt[p] = 0;
+        }
+        // walk on 32 queued particles at once
+        if (qtail - qhead >= 32) {
+            __syncwarp();
+            const WalkItem w = q[(qhead + lane) & (P32_QUEUE - 1)];
+            walk_particle(a, w);
+            qhead += 32;
+            __syncwarp();
+        }
+    }
+    // drain
+    const unsigned left = qtail - qhead;
+    if (left > 0) {
+        __syncwarp();
+        if ((unsigned)lane < left) {
+            const WalkItem w = q[(qhead + lane) & (P32_QUEUE - 1)];
+            walk_particle(a, w);
+        }
+    }
+}
+
+// Persistent grid: resident blocks per SM (from the occupancy calculator) times
+// the SM count, capped by the work.  MINB = minimum resident blocks per SM the
+// register allocation targets (2, 3 or 4 x 256 threads); chosen by `variant`.
+template <int PUSHER, int MINB>
+static void launch_p32(cudaStream_t st, const StepArgs32 &a)
+{
+    static int per_sm = 0, sms = 0, dev = -1;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev || per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32<PUSHER, MINB>, P32_BLOCK, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        dev = d;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long need = (a.nchunks + P32_WARPS - 1) / P32_WARPS;
+    const long long grid = std::min<long long>(need, (long long)per_sm * sms);
+    if (grid <= 0) return;
+    k_particles32<PUSHER, MINB><<<(unsigned)grid, P32_BLOCK, 0, st>>>(a);
+}
+
+template <int PUSHER>
+static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
+{
+    switch (a.variant) {
+    case 2: launch_p32<PUSHER, 2>(st, a); break;
+    case 4: launch_p32<PUSHER, 4>(st, a); break;
+    default: launch_p32<PUSHER, 3>(st, a); break;     // measured best on GB300 (no spills, 24 warps/SM)
     }
 }
 
 void launch_particles32(cudaStream_t st, int pusher, const StepArgs32 &a)
 {
-    if (a.nblocks <= 0) return;
-    const dim3 grid((unsigned)a.nblocks), block(a.block);
+    if (a.nchunks <= 0) return;
     switch (pusher) {
-    case FETDPIC_BORIS: k_particles32<FETDPIC_BORIS><<<grid, block, 0, st>>>(a); break;
-    case FETDPIC_BORIS_TAN: k_particles32<FETDPIC_BORIS_TAN><<<grid, block, 0, st>>>(a); break;
-    case FETDPIC_VAY: k_particles32<FETDPIC_VAY><<<grid, block, 0, st>>>(a); break;
-    default: k_particles32<FETDPIC_HC><<<grid, block, 0, st>>>(a); break;
+    case FETDPIC_BORIS: launch_p32v<FETDPIC_BORIS>(st, a); break;
+    case FETDPIC_BORIS_TAN: launch_p32v<FETDPIC_BORIS_TAN>(st, a); break;
+    case FETDPIC_VAY: launch_p32v<FETDPIC_VAY>(st, a); break;
+    default: launch_p32v<FETDPIC_HC>(st, a); break;
     }
 }
 

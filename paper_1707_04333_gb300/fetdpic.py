@@ -29,7 +29,7 @@ class Params(C.Structure):
     _fields_ = [("eps0", C.c_double), ("mu0", C.c_double), ("c", C.c_double),
                 ("precision", C.c_int), ("spai_level", C.c_int), ("sort_interval", C.c_int),
                 ("max_crossings", C.c_int), ("check_interval", C.c_int), ("record_walk", C.c_int),
-                ("block_size", C.c_int), ("use_graphs", C.c_int), ("time_stages", C.c_int),
+                ("block_size", C.c_int), ("use_graphs", C.c_int), ("time_stages", C.c_int), ("kernel_variant", C.c_int),
                 ("cuda_stream", C.c_void_p),
                 ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p)]
 
@@ -250,7 +250,7 @@ class Simulation:
 
     def __init__(self, workloads, precision="fp64", spai_level=2, sort_interval=16, max_crossings=64,
                  record_walk=0, block_size=0, check_interval=0, use_torch=True, stream=None,
-                 edges=None, edge_tags=None, time_stages=False):
+                 edges=None, edge_tags=None, time_stages=False, kernel_variant=0):
         if not isinstance(workloads, (list, tuple)):
             workloads = [workloads]
         self.workloads = list(workloads)
@@ -264,6 +264,7 @@ class Simulation:
         p.block_size = block_size
         p.check_interval = check_interval
         p.time_stages = 1 if time_stages else 0
+        p.kernel_variant = kernel_variant
         self.stream = None
         if use_torch:
             import torch
