@@ -26,6 +26,7 @@ CU_SOURCES = {
     "kernels_fp64.cu": ["-fmad=false"],
     "kernels_fp32.cu": ["-prec-div=false", "-prec-sqrt=false"],
     "kernels_common.cu": [],
+    "kernels_check.cu": [],
     "fetdpic_api.cu": [],
 }
 CPP_SOURCES = ["mesh_setup.cpp"]

@@ -53,7 +53,8 @@ struct fetdpic_ctx {
     int2 *efac = nullptr; double2 *ecoef = nullptr; int *einst = nullptr;
     double *inst_unit = nullptr, *inst_dt = nullptr;
     int *edge_off_dev = nullptr;
-    long long *m_rp = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
+    long long *m_soff = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
+    float *m_v32 = nullptr, *r32 = nullptr;
     unsigned *status = nullptr;
     std::vector<double> unit_host;           // per instance (q_ref/dt) 2^-shift
     std::vector<int> shift;                  // per instance
@@ -80,6 +81,15 @@ struct fetdpic_ctx {
     std::vector<int> ev_stage;               // stage closed by each recorded event (-1 = start of a step)
     int ev_used = 0;
     double stage_ms[6] = {0, 0, 0, 0, 0, 0};
+    // checks: node -> edge incidence (edge << 1 | enters-node), node instance,
+    // charge in fixed point (q0 before / q1 after the particle kernel), Gauss
+    // reference g0, full [*eps] for the energy, results per instance
+    int *nrp = nullptr, *nedge = nullptr, *ninst = nullptr;
+    unsigned long long *q0 = nullptr, *q1 = nullptr;
+    double *g0 = nullptr, *qunit = nullptr, *chk_out = nullptr, *eng_part = nullptr;
+    long long *h_rp = nullptr; int *h_ci = nullptr; double *h_v = nullptr;
+    bool q_prev_valid = false;                // q0 holds the charge of the current particle state
+    bool g0_ready = false;
     // reusable device scratch for host <-> device transfers of particle state
     void *xfer = nullptr; size_t xfer_bytes = 0;
 
@@ -271,6 +281,68 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         }
     }
     ctx->nfree = (long long)mrow.size();
+    // sliced ELL (32 rows per slice, column-major inside a slice)
+    std::vector<long long> soff(1, 0);
+    std::vector<int> sci;
+    std::vector<double> sv;
+    {
+        const long long nr = ctx->nfree;
+        for (long long s0 = 0; s0 < nr; s0 += 32) {
+            long long wmax = 0;
+            for (long long r = s0; r < std::min(nr, s0 + 32); ++r) wmax = std::max(wmax, mrp[r + 1] - mrp[r]);
+            const long long base = soff.back();
+            sci.resize(base + 32 * wmax);
+            sv.resize(base + 32 * wmax);
+            for (int l = 0; l < 32; ++l) {
+                const long long r = s0 + l;
+                const int pad_col = r < nr ? mrow[r] : (nr > 0 ? mrow[0] : 0);
+                for (long long k = 0; k < wmax; ++k) {
+                    const long long q = base + k * 32 + l;
+                    if (r < nr && k < mrp[r + 1] - mrp[r]) { sci[q] = mci[mrp[r] + k]; sv[q] = mv[mrp[r] + k]; }
+                    else { sci[q] = pad_col; sv[q] = 0.0; }
+                }
+            }
+            soff.push_back(base + 32 * wmax);
+        }
+    }
+    std::vector<float> sv32;
+    if (P.precision == FETDPIC_FP32) { sv32.resize(sv.size()); for (size_t k = 0; k < sv.size(); ++k) sv32[k] = (float)sv[k]; }
+    // node -> edge incidence (fixed order: ascending edge id per node) and the full [*eps]
+    std::vector<int> nrp, nedge, ninst(ctx->N);
+    std::vector<long long> hrp(1, 0);
+    std::vector<int> hci;
+    std::vector<double> hv;
+    if (P.check_interval > 0) {
+        std::vector<int> deg(ctx->N + 1, 0);
+        for (int k = 0; k < n_inst; ++k) {
+            const HostMesh &M = ctx->mesh[k];
+            for (int e = 0; e < M.ne; ++e) {
+                ++deg[ctx->node_off[k] + M.edge[2 * e]];
+                ++deg[ctx->node_off[k] + M.edge[2 * e + 1]];
+            }
+            for (int n = 0; n < M.nn; ++n) ninst[ctx->node_off[k] + n] = k;
+        }
+        nrp.assign(ctx->N + 1, 0);
+        for (int n = 0; n < ctx->N; ++n) nrp[n + 1] = nrp[n] + deg[n];
+        nedge.assign(nrp[ctx->N], 0);
+        std::vector<int> fill(nrp.begin(), nrp.end() - 1);
+        for (int k = 0; k < n_inst; ++k) {
+            const HostMesh &M = ctx->mesh[k];
+            for (int e = 0; e < M.ne; ++e) {
+                const int eg = ctx->edge_off[k] + e;
+                nedge[fill[ctx->node_off[k] + M.edge[2 * e]]++] = eg << 1;            // leaves the node: +1
+                nedge[fill[ctx->node_off[k] + M.edge[2 * e + 1]]++] = (eg << 1) | 1;  // enters the node: -1
+            }
+        }
+        for (int k = 0; k < n_inst; ++k) {
+            const HostMesh &M = ctx->mesh[k];
+            const int eo = ctx->edge_off[k];
+            for (int e = 0; e < M.ne; ++e) {
+                for (long long q = M.h_rp[e]; q < M.h_rp[e + 1]; ++q) { hci.push_back(eo + M.h_ci[q]); hv.push_back(M.h_v[q]); }
+                hrp.push_back((long long)hci.size());
+            }
+        }
+    }
     try {
         ctx->geo64 = ctx->alloc<Geo64>(ctx->F);
         if (P.precision == FETDPIC_FP32) {
@@ -293,15 +365,44 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         ctx->inst_unit = ctx->alloc<double>(n_inst);
         ctx->inst_dt = ctx->alloc<double>(n_inst);
         ctx->edge_off_dev = ctx->alloc<int>(n_inst + 1);
-        ctx->m_rp = ctx->alloc<long long>(mrp.size());
+        ctx->m_soff = ctx->alloc<long long>(soff.size());
         ctx->m_row = ctx->alloc<int>(mrow.size());
-        ctx->m_ci = ctx->alloc<int>(mci.size());
-        ctx->m_v = ctx->alloc<double>(mv.size());
+        ctx->m_ci = ctx->alloc<int>(sci.size());
+        if (P.precision == FETDPIC_FP32) {
+            ctx->m_v32 = ctx->alloc<float>(sv32.size());
+            ctx->r32 = ctx->alloc<float>(ctx->E);
+        } else {
+            ctx->m_v = ctx->alloc<double>(sv.size());
+        }
         ctx->status = ctx->alloc<unsigned>(1);
+        if (P.check_interval > 0) {
+            ctx->nrp = ctx->alloc<int>(nrp.size());
+            ctx->nedge = ctx->alloc<int>(nedge.size());
+            ctx->ninst = ctx->alloc<int>(ninst.size());
+            ctx->q0 = ctx->alloc<unsigned long long>(ctx->N);
+            ctx->q1 = ctx->alloc<unsigned long long>(ctx->N);
+            ctx->g0 = ctx->alloc<double>(ctx->N);
+            ctx->qunit = ctx->alloc<double>(n_inst);
+            ctx->chk_out = ctx->alloc<double>(3 * (size_t)n_inst);
+            ctx->eng_part = ctx->alloc<double>((size_t)energy_blocks(ctx->E, ctx->F) * n_inst);
+            ctx->h_rp = ctx->alloc<long long>(hrp.size());
+            ctx->h_ci = ctx->alloc<int>(hci.size());
+            ctx->h_v = ctx->alloc<double>(hv.size());
+        }
     } catch (const std::bad_alloc &) {
         return FETDPIC_ENOMEM;
     }
     int rc = FETDPIC_OK;
+    if (P.check_interval > 0) {
+        rc = rc ? rc : upload(ctx, ctx->nrp, nrp.data(), nrp.size());
+        rc = rc ? rc : upload(ctx, ctx->nedge, nedge.data(), nedge.size());
+        rc = rc ? rc : upload(ctx, ctx->ninst, ninst.data(), ninst.size());
+        rc = rc ? rc : upload(ctx, ctx->h_rp, hrp.data(), hrp.size());
+        rc = rc ? rc : upload(ctx, ctx->h_ci, hci.data(), hci.size());
+        rc = rc ? rc : upload(ctx, ctx->h_v, hv.data(), hv.size());
+        if (rc) return rc;
+        CK(cudaMemsetAsync(ctx->chk_out, 0, sizeof(double) * 3 * n_inst, ctx->stream));
+    }
     rc = rc ? rc : upload(ctx, ctx->geo64, g64.data(), g64.size());
     if (!g32.empty()) rc = rc ? rc : upload(ctx, ctx->cst32, g32.data(), g32.size());
     if (!dti.empty()) rc = rc ? rc : upload(ctx, ctx->dtinv, dti.data(), dti.size());
@@ -314,10 +415,11 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     rc = rc ? rc : upload(ctx, ctx->einst, einst.data(), einst.size());
     rc = rc ? rc : upload(ctx, ctx->inst_dt, idt.data(), idt.size());
     rc = rc ? rc : upload(ctx, ctx->edge_off_dev, ctx->edge_off.data(), ctx->edge_off.size());
-    rc = rc ? rc : upload(ctx, ctx->m_rp, mrp.data(), mrp.size());
+    rc = rc ? rc : upload(ctx, ctx->m_soff, soff.data(), soff.size());
     rc = rc ? rc : upload(ctx, ctx->m_row, mrow.data(), mrow.size());
-    rc = rc ? rc : upload(ctx, ctx->m_ci, mci.data(), mci.size());
-    rc = rc ? rc : upload(ctx, ctx->m_v, mv.data(), mv.size());
+    rc = rc ? rc : upload(ctx, ctx->m_ci, sci.data(), sci.size());
+    if (P.precision == FETDPIC_FP32) rc = rc ? rc : upload(ctx, ctx->m_v32, sv32.data(), sv32.size());
+    else rc = rc ? rc : upload(ctx, ctx->m_v, sv.data(), sv.size());
     if (rc) return rc;
     CK(cudaMemsetAsync(ctx->ifix, 0, sizeof(unsigned long long) * ctx->E, ctx->stream));
     CK(cudaMemsetAsync(ctx->j, 0, sizeof(double) * ctx->E, ctx->stream));
@@ -353,6 +455,25 @@ extern "C" int fetdpic_load_particles(fetdpic_ctx *ctx, int inst, double q, doub
     }
     ctx->staged.push_back(std::move(s));
     return (int)ctx->staged.size() - 1;
+}
+
+// Charge of the current particle state into q (fixed point).
+static void charge_now(fetdpic_ctx *ctx, unsigned long long *q)
+{
+    launch_charge(ctx->stream, ctx->p.precision == FETDPIC_FP32, ctx->P, ctx->cell, ctx->blk_sp, ctx->block,
+                  ctx->sp_dev, ctx->geo64, ctx->topo, ctx->f[0], ctx->f[1], q, ctx->N);
+}
+
+// The Gauss-law check compares S~ d - q with its value at this point (after
+// load, or after a state is written from the host).
+static void reset_gauss_reference(fetdpic_ctx *ctx)
+{
+    if (!ctx->g0 || !ctx->finalized) { ctx->q_prev_valid = false; return; }
+    charge_now(ctx, ctx->q0);
+    launch_dgl(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->qunit, ctx->d, ctx->q0, ctx->g0, 1,
+               ctx->chk_out);
+    ctx->q_prev_valid = true;
+    ctx->g0_ready = true;
 }
 
 // Move the staged species to the device: padded species ranges, block ->
@@ -500,10 +621,17 @@ static int finalize(fetdpic_ctx *ctx)
     rc = rc ? rc : upload(ctx, ctx->hoff, hoff.data(), hoff.size());
     rc = rc ? rc : upload(ctx, ctx->pad_adj, pad_adj.data(), pad_adj.size());
     rc = rc ? rc : upload(ctx, ctx->inst_unit, ctx->unit_host.data(), ctx->unit_host.size());
+    if (ctx->qunit) {
+        std::vector<double> qu(ni);
+        for (int k = 0; k < ni; ++k) qu[k] = (qref[k] > 0 ? qref[k] : 1.0) * std::ldexp(1.0, -ctx->shift[k]);
+        rc = rc ? rc : upload(ctx, ctx->qunit, qu.data(), qu.size());
+    }
     if (rc) return rc;
     if (ctx->rec_cnt) CK(cudaMemsetAsync(ctx->rec_cnt, 0, sizeof(int) * ctx->P, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->finalized = true;
+    reset_gauss_reference(ctx);
+    CK(cudaStreamSynchronize(ctx->stream));
     return FETDPIC_OK;
 }
 
@@ -594,21 +722,42 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
     launches += ctx->F > 0;
     if (timed) mark(ctx, 0);
+    const bool check = ctx->p.check_interval > 0 && ctx->g0 &&
+                       ((ctx->steps_done + 1) % ctx->p.check_interval == 0);
+    if (check && !ctx->q_prev_valid) { charge_now(ctx, ctx->q0); launches += 2; }
     if (ctx->nblocks > 0) {
         if (f32) launch_particles32(ctx->stream, pusher, args32(ctx));
         else launch_particles64(ctx->stream, pusher, args64(ctx));
         ++launches;
     }
     if (timed) mark(ctx, 1);
+    if (check) {
+        charge_now(ctx, ctx->q1);
+        launch_dce(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->ifix, ctx->q0, ctx->q1, ctx->chk_out);
+        launches += 3;
+    }
     AmpereArgs A{};
     A.E = ctx->E; A.efac = ctx->efac; A.ecoef = ctx->ecoef; A.einst = ctx->einst;
     A.inst_unit = ctx->inst_unit; A.inst_dt = ctx->inst_dt; A.b = ctx->b; A.ifix = ctx->ifix;
-    A.r = ctx->r; A.d = ctx->d; A.j = ctx->j;
-    A.nfree = ctx->nfree; A.m_rp = ctx->m_rp; A.m_row = ctx->m_row; A.m_ci = ctx->m_ci; A.m_v = ctx->m_v;
+    A.r = ctx->r; A.d = ctx->d; A.j = ctx->j; A.r32 = ctx->r32;
+    A.nfree = ctx->nfree; A.m_soff = ctx->m_soff; A.m_row = ctx->m_row; A.m_ci = ctx->m_ci; A.m_v = ctx->m_v;
+    A.m_v32 = ctx->m_v32;
     A.e = ctx->e;
     launch_ampere(ctx->stream, A);
     launches += (ctx->E > 0) + (ctx->nfree > 0);
     if (timed) mark(ctx, 3);
+    if (check) {
+        launch_dgl(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->qunit, ctx->d, ctx->q1, ctx->g0, 0,
+                   ctx->chk_out);
+        launch_energy(ctx->stream, ctx->E, ctx->F, ctx->h_rp, ctx->h_ci, ctx->h_v, ctx->e, ctx->einst, ctx->b,
+                      ctx->geo64, ctx->topo, (int)ctx->mesh.size(), ctx->eng_part, ctx->chk_out);
+        launches += 3;
+        std::swap(ctx->q0, ctx->q1);          // the charge after this step is the next step's q^n
+        ctx->q_prev_valid = true;
+        if (timed) mark(ctx, 5);
+    } else {
+        ctx->q_prev_valid = false;
+    }
     ++ctx->steps_done;
     if (ctx->p.sort_interval > 0 && ctx->nblocks > 0 && ctx->steps_done % ctx->p.sort_interval == 0) {
         do_sort(ctx);
@@ -705,6 +854,8 @@ extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const doub
                   1.0 / ctx->p.c, ctx->cell, ctx->id, ctx->f[0], ctx->f[1], ctx->f[2], ctx->f[3]);
     CK(cudaGetLastError());
     if (!cell) CK(cudaStreamSynchronize(ctx->stream));   // `located` goes out of scope
+    ctx->q_prev_valid = false;
+    if (ctx->g0) reset_gauss_reference(ctx);
     return FETDPIC_OK;
 }
 
@@ -730,6 +881,7 @@ extern "C" int fetdpic_write_fields(fetdpic_ctx *ctx, int inst, const double *e,
         if (rc) return rc;
         CK(cudaStreamSynchronize(ctx->stream));
     }
+    if (e) reset_gauss_reference(ctx);
     return FETDPIC_OK;
 }
 
@@ -806,8 +958,17 @@ extern "C" int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *r
 extern "C" int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double *dgl_max, double *energy)
 {
     if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
-    (void)dce_max; (void)dgl_max; (void)energy;
-    return ctx->fail(FETDPIC_ESTATE, "checks are not enabled in this build");
+    if (!ctx->chk_out) return ctx->fail(FETDPIC_ESTATE, "check_interval is 0: no checks are computed");
+    CK(cudaStreamSynchronize(ctx->stream));
+    double v[3] = {0, 0, 0};
+    CK(cudaMemcpy(v, ctx->chk_out + 3 * inst, sizeof(v), cudaMemcpyDeviceToHost));
+    if (dce_max) *dce_max = v[0];
+    if (dgl_max) *dgl_max = v[1];
+    if (energy) *energy = v[2];
+    CK(cudaMemset(ctx->chk_out + 3 * inst, 0, 2 * sizeof(double)));   // maxima restart; energy stays
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return map_status(ctx, st);
 }
 
 extern "C" int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6])

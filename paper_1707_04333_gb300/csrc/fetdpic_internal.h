@@ -155,8 +155,10 @@ struct AmpereArgs {
     const double *b;
     unsigned long long *ifix;                 // read and cleared
     double *r, *d, *j;
+    float *r32;                               // FP32 copy of r (FP32 path), or null
     long long nfree;
-    const long long *m_rp; const int *m_row; const int *m_ci; const double *m_v;  // dt-scaled SPAI
+    // dt-scaled SPAI in sliced ELL: slice offsets, row -> edge, columns, values (FP64 or FP32)
+    const long long *m_soff; const int *m_row; const int *m_ci; const double *m_v; const float *m_v32;
     double *e;
 };
 void launch_ampere(cudaStream_t st, const AmpereArgs &a);
@@ -177,6 +179,19 @@ struct SortArgs {
 };
 void launch_sort(cudaStream_t st, const SortArgs &a);
 
+
+// Conservation checks (kernels_check.cu).
+void launch_charge(cudaStream_t st, bool fp32, long long P, const int *cell, const short *blk_sp, int block,
+                   const Species *sp, const Geo64 *geo, const Topo *topo, const void *f0, const void *f1,
+                   unsigned long long *q, int N);
+void launch_dce(cudaStream_t st, int N, const int *nrp, const int *nedge, const int *ninst,
+                const unsigned long long *ifix, const unsigned long long *q0, const unsigned long long *q1, double *out);
+void launch_dgl(cudaStream_t st, int N, const int *nrp, const int *nedge, const int *ninst, const double *qunit,
+                const double *d, const unsigned long long *q, double *g0, int init, double *out);
+long long energy_blocks(int E, int F);
+void launch_energy(cudaStream_t st, int E, int F, const long long *hrp, const int *hci, const double *hv,
+                   const double *e, const int *einst, const double *b, const Geo64 *geo, const Topo *topo,
+                   int ninst, double *part, double *out);
 
 size_t scan_tmp_ints(long long n);
 void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n, int *tmp);

@@ -15,7 +15,7 @@ __global__ void k_curl_h(int E, const int2 *__restrict__ efac, const double2 *__
                          const int *__restrict__ einst, const double *__restrict__ unit,
                          const double *__restrict__ idt, const double *__restrict__ b,
                          unsigned long long *__restrict__ ifix, double *__restrict__ r,
-                         double *__restrict__ d, double *__restrict__ j)
+                         float *__restrict__ r32, double *__restrict__ d, double *__restrict__ j)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
@@ -29,38 +29,47 @@ __global__ void k_curl_h(int E, const int2 *__restrict__ efac, const double2 *__
     const double cur = (double)iv * unit[in];
     const double rv = h - cur;
     r[e] = rv;
+    if (r32) r32[e] = (float)rv;
     j[e] = cur;
     d[e] += idt[in] * rv;
 }
 
-// e_free += (dt M) r: SpMV with the dt-scaled SPAI, 8 lanes per row.
-__global__ void k_spai_spmv(long long nrows, const long long *__restrict__ rp, const int *__restrict__ row_edge,
-                            const int *__restrict__ ci, const double *__restrict__ v,
-                            const double *__restrict__ r, double *__restrict__ e)
+// e_free += (dt M) r: SpMV with the dt-scaled SPAI in sliced ELL (slices of
+// 32 rows, each padded to its longest row and stored column-major, so a warp
+// reads 32 consecutive column indices and values per step).  One thread per
+// row; padding entries have value 0 and a valid column.
+template <typename V>
+__global__ void __launch_bounds__(256) k_spai_sell(long long nrows, const long long *__restrict__ soff,
+                                                   const int *__restrict__ row_edge, const int *__restrict__ ci,
+                                                   const V *__restrict__ v, const V *__restrict__ r,
+                                                   double *__restrict__ e)
 {
-    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long row = gid >> 3;
-    const int sub = threadIdx.x & 7;
-    double s = 0.0;
-    if (row < nrows) {
-        const long long lo = rp[row], hi = rp[row + 1];
-        for (long long q = lo + sub; q < hi; q += 8) s += v[q] * r[ci[q]];
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nrows) return;
+    const long long sl = row >> 5;
+    const int lane = (int)(row & 31);
+    const long long o0 = soff[sl], o1 = soff[sl + 1];
+    V s0 = V(0), s1 = V(0);
+    long long q = o0 + lane;
+    for (; q + 32 < o1; q += 64) {
+        s0 += v[q] * r[ci[q]];
+        s1 += v[q + 32] * r[ci[q + 32]];
     }
-    s += __shfl_down_sync(0xffffffffu, s, 4, 8);
-    s += __shfl_down_sync(0xffffffffu, s, 2, 8);
-    s += __shfl_down_sync(0xffffffffu, s, 1, 8);
-    if (row < nrows && sub == 0) e[row_edge[row]] += s;
+    if (q < o1) s0 += v[q] * r[ci[q]];
+    e[row_edge[row]] += (double)(s0 + s1);
 }
 
 void launch_ampere(cudaStream_t st, const AmpereArgs &a)
 {
     if (a.E > 0)
         k_curl_h<<<(a.E + 255) / 256, 256, 0, st>>>(a.E, a.efac, a.ecoef, a.einst, a.inst_unit, a.inst_dt,
-                                                     a.b, a.ifix, a.r, a.d, a.j);
+                                                     a.b, a.ifix, a.r, a.r32, a.d, a.j);
     if (a.nfree > 0) {
-        const long long threads = a.nfree * 8;
-        k_spai_spmv<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a.nfree, a.m_rp, a.m_row, a.m_ci, a.m_v,
-                                                                       a.r, a.e);
+        const unsigned g = (unsigned)((a.nfree + 255) / 256);
+        if (a.m_v32)
+            k_spai_sell<float><<<g, 256, 0, st>>>(a.nfree, a.m_soff, a.m_row, a.m_ci, a.m_v32, a.r32, a.e);
+        else
+            k_spai_sell<double><<<g, 256, 0, st>>>(a.nfree, a.m_soff, a.m_row, a.m_ci, a.m_v, a.r, a.e);
     }
 }
 
