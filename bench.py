@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
-    ap.add_argument("--variant", type=int, default=0, help="FP32 particle-kernel variant (0 = library default)")
+    ap.add_argument("--variant", type=int, default=0, help="FP32 particle-kernel variant (0 = autotuned)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the library defaults instead of autotuning")
     return ap.parse_args()
 
 
@@ -65,7 +66,7 @@ def workload(args):
 def describe(w, args, precision):
     nf = len(w.mesh.triangles)
     return (f"pair-plasma {nf} triangles, {w.n_particles} particles (e+p, {args.ppc}/species/triangle), "
-            f"{args.pusher}, {precision}, sort every {args.sort_interval}")
+            f"{args.pusher}, {precision}")
 
 
 def peaks():
@@ -202,6 +203,12 @@ def main():
         sim = fetdpic.Simulation(w, precision=precision, spai_level=2, sort_interval=args.sort_interval,
                                  time_stages=stages, stream=stream, kernel_variant=args.variant)
         sim.load()
+        if args.variant == 0 and not args.no_tune:
+            tuned = sim.autotune(args.pusher, trial_steps=32,
+                                 cache=os.path.join(ROOT, "paper_1707_04333_gb300", "_build", "tuning.json"))
+        else:
+            tuned = (args.variant, args.sort_interval)
+        sim.tuned = tuned
         sim.step(warmup, args.pusher).sync()
         fetdpic.fetdpic_stage_times(sim.h)            # reset the sums
         barrier()
@@ -282,6 +289,7 @@ def main():
             te = float(t.item())
         e2e = {"value": npart * ke * world / te, "unit": UNIT, "h2d_bytes_per_step": int(npart * 36),
                "d2h_bytes_per_step": int(npart * 36), "steps": ke}
+    sim_tuned = sim.tuned
     sim.close()
     del sim
 
@@ -315,6 +323,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(w, args, "fp32 cell-local barycentric"),
+                       "tuning": {"kernel_variant": sim_tuned[0], "sort_interval": sim_tuned[1]},
                        "triangles": len(w.mesh.triangles), "particles_per_gpu": npart,
                        "l2": "inputs larger than L2 (particle state 2 x 161 MB per step)",
                        "parallelism": f"replicas x{world}"},

@@ -221,6 +221,20 @@ int fetdpic_read_edges(fetdpic_ctx *ctx, int inst, int *edges);
  * (edge id), val [nnz]; row_edge [n_free].  Any NULL output is skipped. */
 int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_edge, int *col, double *val);
 
+/* Autotuner (no counterpart in the paper, which reports no kernels): times
+ * short trials of every (FP32 particle-kernel variant in {2, 3, 4}) x (sort
+ * interval in {8, 16, 32}) combination -- only the sort interval for FP64,
+ * nothing if sorting is off -- starting each from the current state, keeps
+ * the fastest per step (sort cost included), and restores the particle and
+ * field state exactly, so the simulation is unchanged.  trial_steps <= 0 =
+ * 32.  The chosen values are returned in *variant and *sort_interval (each
+ * may be NULL) and applied.  Blocks the calling thread. */
+int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, int *variant, int *sort_interval);
+
+/* Apply a tuning found earlier (e.g. from a cache): variant 0, 2, 3 or 4;
+ * sort_interval > 0, or < 0 for never. */
+int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval);
+
 /* Device time per stage, summed over every step enqueued since the previous
  * call (needs time_stages = 1; CUDA events recorded on the context stream
  * between stages, read at fetdpic_sync): out[0] Faraday + field record,

@@ -93,12 +93,18 @@ struct fetdpic_ctx {
     // reusable device scratch for host <-> device transfers of particle state
     void *xfer = nullptr; size_t xfer_bytes = 0;
 
+    // captured one-step graphs: [pusher][particle-buffer parity][step sorts]
+    cudaGraphExec_t graph[4][2][2] = {};
+    long long graph_launches[4][2][2] = {};
+    int *cell_a = nullptr;                    // the first particle buffer (parity reference)
+
     std::vector<void *> allocs;
 
     ~fetdpic_ctx()
     {
         cudaSetDevice(device);
         if (stream) cudaStreamSynchronize(stream);
+        for (auto &a : graph) for (auto &b : a) for (auto &g : b) if (g) cudaGraphExecDestroy(g);
         for (void *q : allocs) {
             if (p.dev_free) p.dev_free(q, p.alloc_user);
             else cudaFree(q);
@@ -558,6 +564,7 @@ static int finalize(fetdpic_ctx *ctx)
         ctx->sp32_dev = ctx->alloc<Sp32>(s32.size());
         ctx->sp_dev = ctx->alloc<Species>(std::max(ns, 1));
         ctx->cell = ctx->alloc<int>(ctx->P);
+        ctx->cell_a = ctx->cell;
         ctx->cell_tmp = ctx->alloc<int>(ctx->P);
         ctx->id = ctx->alloc<int>(ctx->P);
         ctx->id_tmp = ctx->alloc<int>(ctx->P);
@@ -704,6 +711,7 @@ static void do_sort(fetdpic_ctx *ctx)
     s.fbytes = ctx->p.precision == FETDPIC_FP32 ? 4 : 8;
     s.hist = ctx->hist; s.hoff = ctx->hoff; s.hist_n = ctx->hist_n; s.scan_tmp = ctx->scan_tmp;
     s.pad_adj_dev = ctx->pad_adj; s.blk_sp = ctx->blk_sp; s.nblocks = ctx->nblocks; s.block = ctx->block;
+    s.chunk_sp = ctx->chunk_sp;
     launch_sort(ctx->stream, s);
     std::swap(ctx->cell, ctx->cell_tmp);
     std::swap(ctx->id, ctx->id_tmp);
@@ -767,6 +775,43 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     return launches;
 }
 
+// One step through a captured graph: the launch sequence of a step depends only
+// on the pusher, which particle buffer is current and whether the step sorts,
+// so each combination is captured once (capture enqueues nothing; the host-side
+// bookkeeping of the step happens during capture) and replayed.
+static int graph_step(fetdpic_ctx *ctx, int pusher, long long &launches)
+{
+    const bool sorts = ctx->p.sort_interval > 0 && ctx->nblocks > 0 &&
+                       (ctx->steps_done + 1) % ctx->p.sort_interval == 0;
+    const int parity = ctx->cell == ctx->cell_a ? 0 : 1;
+    cudaGraphExec_t &g = ctx->graph[pusher][parity][sorts ? 1 : 0];
+    if (!g) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        const long long n = enqueue_step(ctx, pusher, false);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { g = nullptr; return ctx->cuda_fail(e, "cudaGraphInstantiate"); }
+        ctx->graph_launches[pusher][parity][sorts ? 1 : 0] = n;
+        CK(cudaGraphLaunch(g, ctx->stream));
+        launches += n;
+        return FETDPIC_OK;
+    }
+    CK(cudaGraphLaunch(g, ctx->stream));
+    launches += ctx->graph_launches[pusher][parity][sorts ? 1 : 0];
+    // host-side effects of the step the graph replays
+    ++ctx->steps_done;
+    ctx->q_prev_valid = false;
+    if (sorts) {
+        std::swap(ctx->cell, ctx->cell_tmp);
+        std::swap(ctx->id, ctx->id_tmp);
+        for (int k = 0; k < 4; ++k) std::swap(ctx->f[k], ctx->f_tmp[k]);
+    }
+    return FETDPIC_OK;
+}
+
 extern "C" int fetdpic_step(fetdpic_ctx *ctx, long long nsteps, int pusher)
 {
     if (!ctx) return FETDPIC_EINVAL;
@@ -781,7 +826,13 @@ extern "C" int fetdpic_step(fetdpic_ctx *ctx, long long nsteps, int pusher)
     }
     long long launches = 0;
     const bool timed = ctx->p.time_stages != 0;
+    const bool graphs = ctx->p.use_graphs != 0 && !timed && ctx->p.check_interval <= 0;
     for (long long s = 0; s < nsteps; ++s) {
+        if (graphs) {
+            rc = graph_step(ctx, pusher, launches);
+            if (rc) return rc;
+            continue;
+        }
         if (timed && ctx->ev_used > 4000) {
             CK(cudaStreamSynchronize(ctx->stream));
             collect_events(ctx);
@@ -999,6 +1050,112 @@ extern "C" int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, 
     if (row_edge) std::memcpy(row_edge, M.free_edges.data(), sizeof(int) * M.free_edges.size());
     if (col) std::memcpy(col, M.m_ci.data(), sizeof(int) * M.m_ci.size());
     if (val) std::memcpy(val, M.m_v.data(), sizeof(double) * M.m_v.size());
+    return FETDPIC_OK;
+}
+
+// ------------------------------------------------------------ autotuning
+
+static void drop_graphs(fetdpic_ctx *ctx)
+{
+    for (auto &a : ctx->graph) for (auto &b : a) for (auto &g : b) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    if (variant < 0 || variant > 4 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->p.kernel_variant = variant;
+    ctx->p.sort_interval = sort_interval;
+    drop_graphs(ctx);
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, int *variant, int *sort_interval)
+{
+    if (!ctx || pusher < 0 || pusher > 3) return FETDPIC_EINVAL;
+    int rc = finalize(ctx);
+    if (rc) return rc;
+    if (trial_steps <= 0) trial_steps = 32;
+    CK(cudaStreamSynchronize(ctx->stream));
+    // save the state the trials disturb
+    const size_t fb = ctx->p.precision == FETDPIC_FP32 ? 4 : 8;
+    const size_t pbytes = (size_t)ctx->P * (8 + 4 * fb);
+    const size_t fbytes = sizeof(double) * (2 * (size_t)ctx->E + ctx->F);
+    char *save = nullptr;
+    try { save = ctx->alloc<char>(pbytes + fbytes); } catch (const std::bad_alloc &) { return FETDPIC_ENOMEM; }
+    auto copy_state = [&](bool to_save) -> int {
+        char *q = save;
+        void *dst[8], *src[8];
+        size_t n[8];
+        int k = 0;
+        dst[k] = ctx->cell; n[k++] = sizeof(int) * ctx->P;
+        dst[k] = ctx->id; n[k++] = sizeof(int) * ctx->P;
+        for (int a = 0; a < 4; ++a) { dst[k] = ctx->f[a]; n[k++] = fb * ctx->P; }
+        dst[k] = ctx->e; n[k++] = sizeof(double) * ctx->E;
+        dst[k] = ctx->d; n[k++] = sizeof(double) * ctx->E;
+        for (int a = 0; a < k; ++a) { src[a] = q; q += n[a]; }
+        for (int a = 0; a < k; ++a) {
+            if (to_save) CK(cudaMemcpyAsync(src[a], dst[a], n[a], cudaMemcpyDeviceToDevice, ctx->stream));
+            else CK(cudaMemcpyAsync(dst[a], src[a], n[a], cudaMemcpyDeviceToDevice, ctx->stream));
+        }
+        if (to_save) CK(cudaMemcpyAsync(q, ctx->b, sizeof(double) * ctx->F, cudaMemcpyDeviceToDevice, ctx->stream));
+        else CK(cudaMemcpyAsync(ctx->b, q, sizeof(double) * ctx->F, cudaMemcpyDeviceToDevice, ctx->stream));
+        return FETDPIC_OK;
+    };
+    const int keep_variant = ctx->p.kernel_variant, keep_sort = ctx->p.sort_interval;
+    const bool keep_timed = ctx->p.time_stages != 0;
+    const int keep_check = ctx->p.check_interval;
+    const long long keep_steps = ctx->steps_done;
+    ctx->p.time_stages = 0;
+    ctx->p.check_interval = 0;
+    rc = copy_state(true);
+    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4} : std::vector<int>{3};
+    std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 16, 32};
+    double best = 1e300;
+    int bv = keep_variant, bs = keep_sort;
+    cudaEvent_t t0, t1;
+    CK(cudaEventCreate(&t0));
+    CK(cudaEventCreate(&t1));
+    for (int v : variants)
+        for (int si : sorts) {
+            if (rc) break;
+            rc = copy_state(false);
+            if (rc) break;
+            ctx->p.kernel_variant = v;
+            ctx->p.sort_interval = si;
+            ctx->steps_done = 0;
+            const int n = si > 0 ? std::max(trial_steps, si) / si * si : trial_steps;
+            enqueue_step(ctx, pusher, false);                           // warm-up
+            CK(cudaEventRecord(t0, ctx->stream));
+            for (int k = 0; k < n; ++k) enqueue_step(ctx, pusher, false);
+            CK(cudaEventRecord(t1, ctx->stream));
+            CK(cudaEventSynchronize(t1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, t0, t1));
+            if (ms / n < best) { best = ms / n; bv = v; bs = si; }
+        }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    // back to the saved state; the trials' currents are discarded
+    if (!rc) rc = copy_state(false);
+    CK(cudaMemsetAsync(ctx->ifix, 0, sizeof(unsigned long long) * ctx->E, ctx->stream));
+    CK(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (size_t k = 0; k < ctx->allocs.size(); ++k)
+        if (ctx->allocs[k] == save) { ctx->allocs.erase(ctx->allocs.begin() + k); break; }
+    if (ctx->p.dev_free) ctx->p.dev_free(save, ctx->p.alloc_user);
+    else cudaFree(save);
+    ctx->p.time_stages = keep_timed ? 1 : 0;
+    ctx->p.check_interval = keep_check;
+    ctx->steps_done = keep_steps;
+    ctx->q_prev_valid = false;
+    if (rc) { ctx->p.kernel_variant = keep_variant; ctx->p.sort_interval = keep_sort; return rc; }
+    ctx->p.kernel_variant = bv;
+    ctx->p.sort_interval = bs;
+    drop_graphs(ctx);
+    if (variant) *variant = bv;
+    if (sort_interval) *sort_interval = bs;
     return FETDPIC_OK;
 }
 

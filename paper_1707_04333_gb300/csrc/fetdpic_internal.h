@@ -176,6 +176,7 @@ struct SortArgs {
     int *scan_tmp;                            // scratch for the block sums
     const long long *pad_adj_dev;             // per species storage_off - packed_off
     const short *blk_sp; long long nblocks; int block;
+    const short *chunk_sp;                    // species of each 32-particle chunk
 };
 void launch_sort(cudaStream_t st, const SortArgs &a);
 

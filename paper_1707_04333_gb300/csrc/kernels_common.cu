@@ -1,5 +1,7 @@
 // Field-update (Ampere) kernels, the counting sort of particles by triangle,
 // the scan it needs, and the kernels that return particles in load order.
+#include <type_traits>
+
 #include <cuda_runtime.h>
 
 #include "fetdpic_internal.h"
@@ -158,45 +160,66 @@ void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n
 // of particles inside one triangle depends on atomic order; nothing computed
 // depends on it (the deposit is integer, reads go through the id array).
 
+// Histogram: one integer atomic per run of equal triangle in a warp.
 __global__ void k_hist(const int *__restrict__ cell, const short *__restrict__ blk_sp, const Species *__restrict__ sp,
                        const int *__restrict__ hoff, int *__restrict__ hist)
 {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = cell[p];
-    if (c < 0) return;
     const int s = blk_sp[blockIdx.x];
-    atomicAdd(hist + hoff[s] + (c - sp[s].cell_off), 1);
+    const int slot = c < 0 ? -1 : hoff[s] + (c - sp[s].cell_off);
+    const unsigned peers = __match_any_sync(0xffffffffu, slot);
+    if (slot >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + slot, __popc(peers));
 }
 
+// Scatter through per-triangle cursors.  Each warp handles SC_CHUNKS
+// consecutive 32-particle chunks: all cursor atomics are issued before any of
+// their results is used, then the payload moves.
+constexpr int SC_CHUNKS = 4;
+
 template <int FB>
-__global__ void k_scatter(const int *__restrict__ cell, const int *__restrict__ id,
-                          const short *__restrict__ blk_sp, const Species *__restrict__ sp,
-                          const int *__restrict__ hoff, int *__restrict__ cursor,
-                          const long long *__restrict__ pad_adj,
-                          const void *f0, const void *f1, const void *f2, const void *f3,
-                          int *__restrict__ cell_o, int *__restrict__ id_o,
-                          void *g0, void *g1, void *g2, void *g3)
+__global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *__restrict__ cell,
+                                                 const int *__restrict__ id, const short *__restrict__ chunk_sp,
+                                                 const Species *__restrict__ sp, const int *__restrict__ hoff,
+                                                 int *__restrict__ cursor, const long long *__restrict__ pad_adj,
+                                                 const void *f0, const void *f1, const void *f2, const void *f3,
+                                                 int *__restrict__ cell_o, int *__restrict__ id_o,
+                                                 void *g0, void *g1, void *g2, void *g3)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = cell[p];
-    if (c < 0) return;
-    const int s = blk_sp[blockIdx.x];
-    const int slot = hoff[s] + (c - sp[s].cell_off);
-    // warp-aggregated cursor increments for particles of the same triangle
-    const unsigned peers = __match_any_sync(__activemask(), slot);
-    const int leader = __ffs(peers) - 1;
-    const int rank = __popc(peers & ((1u << (threadIdx.x & 31)) - 1u));
-    int base = 0;
-    if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(cursor + slot, __popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    const long long q = (long long)(base + rank) + pad_adj[s];
-    cell_o[q] = c;
-    id_o[q] = id[p];
     using T = typename std::conditional<FB == 8, double, float>::type;
-    ((T *)g0)[q] = ((const T *)f0)[p];
-    ((T *)g1)[q] = ((const T *)f1)[p];
-    ((T *)g2)[q] = ((const T *)f2)[p];
-    ((T *)g3)[q] = ((const T *)f3)[p];
+    const int lane = threadIdx.x & 31;
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long c0 = w * SC_CHUNKS;
+    int cc[SC_CHUNKS], slot[SC_CHUNKS], sid[SC_CHUNKS], base[SC_CHUNKS], rank[SC_CHUNKS];
+    unsigned peers[SC_CHUNKS];
+#pragma unroll
+    for (int k = 0; k < SC_CHUNKS; ++k) {
+        const long long ch = c0 + k;
+        cc[k] = -1; sid[k] = 0;
+        if (ch < nchunks) { cc[k] = cell[ch * 32 + lane]; sid[k] = chunk_sp[ch]; }
+    }
+#pragma unroll
+    for (int k = 0; k < SC_CHUNKS; ++k) {
+        slot[k] = cc[k] < 0 ? -1 : hoff[sid[k]] + (cc[k] - sp[sid[k]].cell_off);
+        peers[k] = __match_any_sync(0xffffffffu, slot[k]);
+        rank[k] = __popc(peers[k] & ((1u << lane) - 1u));
+        base[k] = 0;
+        if (slot[k] >= 0 && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(cursor + slot[k], __popc(peers[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < SC_CHUNKS; ++k) {
+        const int leader = __ffs(peers[k]) - 1;
+        const int b = __shfl_sync(0xffffffffu, base[k], leader);
+        if (slot[k] < 0) continue;
+        const long long p = (c0 + k) * 32 + lane;
+        const long long q = (long long)(b + rank[k]) + pad_adj[sid[k]];
+        cell_o[q] = cc[k];
+        id_o[q] = id[p];
+        ((T *)g0)[q] = ((const T *)f0)[p];
+        ((T *)g1)[q] = ((const T *)f1)[p];
+        ((T *)g2)[q] = ((const T *)f2)[p];
+        ((T *)g3)[q] = ((const T *)f3)[p];
+    }
 }
 
 void launch_sort(cudaStream_t st, const SortArgs &a)
@@ -205,16 +228,17 @@ void launch_sort(cudaStream_t st, const SortArgs &a)
     k_hist<<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.blk_sp, a.sp_dev, a.hoff, a.hist);
     // exclusive scan in place into the cursor array (hist doubles as cursor)
     launch_exclusive_scan(st, a.hist, a.hist, a.hist_n, a.scan_tmp);
+    const long long nchunks = a.P / 32;
+    const long long warps = (nchunks + SC_CHUNKS - 1) / SC_CHUNKS;
+    const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
     if (a.fbytes == 8)
-        k_scatter<8><<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.id, a.blk_sp, a.sp_dev, a.hoff, a.hist,
-                                                              a.pad_adj_dev, a.f[0], a.f[1], a.f[2], a.f[3],
-                                                              a.cell_tmp, a.id_tmp, a.f_tmp[0], a.f_tmp[1],
-                                                              a.f_tmp[2], a.f_tmp[3]);
+        k_scatter<8><<<grid, 256, 0, st>>>(nchunks, a.cell, a.id, a.chunk_sp, a.sp_dev, a.hoff, a.hist, a.pad_adj_dev,
+                                           a.f[0], a.f[1], a.f[2], a.f[3], a.cell_tmp, a.id_tmp, a.f_tmp[0],
+                                           a.f_tmp[1], a.f_tmp[2], a.f_tmp[3]);
     else
-        k_scatter<4><<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.id, a.blk_sp, a.sp_dev, a.hoff, a.hist,
-                                                              a.pad_adj_dev, a.f[0], a.f[1], a.f[2], a.f[3],
-                                                              a.cell_tmp, a.id_tmp, a.f_tmp[0], a.f_tmp[1],
-                                                              a.f_tmp[2], a.f_tmp[3]);
+        k_scatter<4><<<grid, 256, 0, st>>>(nchunks, a.cell, a.id, a.chunk_sp, a.sp_dev, a.hoff, a.hist, a.pad_adj_dev,
+                                           a.f[0], a.f[1], a.f[2], a.f[3], a.cell_tmp, a.id_tmp, a.f_tmp[0],
+                                           a.f_tmp[1], a.f_tmp[2], a.f_tmp[3]);
 }
 
 // ------------------------------------------------------------ load order

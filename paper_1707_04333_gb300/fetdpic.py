@@ -79,6 +79,8 @@ def lib():
             "fetdpic_read_edges": (i32, [vp, i32, vp]),
             "fetdpic_read_spai": (i32, [vp, i32, vp, vp, vp, vp]),
             "fetdpic_stage_times": (i32, [vp, vp, vp]),
+            "fetdpic_autotune": (i32, [vp, i32, i32, vp, vp]),
+            "fetdpic_set_tuning": (i32, [vp, i32, i32]),
             "fetdpic_particle_bytes": (i32, [vp, vp, vp]),
             "fetdpic_last_error": (C.c_char_p, [vp]),
             "fetdpic_destroy": (None, [vp]),
@@ -215,6 +217,18 @@ def fetdpic_stage_times(h):
     return out, n.value
 
 
+def fetdpic_autotune(h, pusher, trial_steps=32):
+    p = PUSHERS[pusher] if isinstance(pusher, str) else int(pusher)
+    v = C.c_int()
+    s = C.c_int()
+    _check(h, lib().fetdpic_autotune(h, p, trial_steps, C.byref(v), C.byref(s)))
+    return v.value, s.value
+
+
+def fetdpic_set_tuning(h, variant, sort_interval):
+    return _check(h, lib().fetdpic_set_tuning(h, variant, sort_interval))
+
+
 def fetdpic_particle_bytes(h):
     b = C.c_double()
     n = C.c_longlong()
@@ -250,7 +264,7 @@ class Simulation:
 
     def __init__(self, workloads, precision="fp64", spai_level=2, sort_interval=16, max_crossings=64,
                  record_walk=0, block_size=0, check_interval=0, use_torch=True, stream=None,
-                 edges=None, edge_tags=None, time_stages=False, kernel_variant=0):
+                 edges=None, edge_tags=None, time_stages=False, kernel_variant=0, use_graphs=False):
         if not isinstance(workloads, (list, tuple)):
             workloads = [workloads]
         self.workloads = list(workloads)
@@ -265,6 +279,7 @@ class Simulation:
         p.check_interval = check_interval
         p.time_stages = 1 if time_stages else 0
         p.kernel_variant = kernel_variant
+        p.use_graphs = 1 if use_graphs else 0
         self.stream = None
         if use_torch:
             import torch
@@ -321,6 +336,39 @@ class Simulation:
     def sync(self):
         fetdpic_sync(self.h)
         return self
+
+    def autotune(self, pusher=None, trial_steps=32, cache=None):
+        """Pick the particle-kernel variant and sort interval by timing trials (state restored),
+        or reuse a choice cached in the JSON file `cache` under (GPU, workload shape, precision,
+        pusher).  Returns (variant, sort_interval)."""
+        import json
+        import torch
+        pusher = pusher or self.workloads[0].pusher
+        key = "|".join([torch.cuda.get_device_name(), self.workloads_signature(), str(self.params.precision),
+                        pusher])
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                table = json.load(open(cache))
+            except (OSError, ValueError):
+                table = {}
+        if key in table:
+            v, s = table[key]
+            fetdpic_set_tuning(self.h, v, s)
+            return v, s
+        v, s = fetdpic_autotune(self.h, pusher, trial_steps)
+        if cache:
+            table[key] = [v, s]
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return v, s
+
+    def workloads_signature(self):
+        tri = sum(len(w.mesh.triangles) for w in self.workloads)
+        par = sum(w.n_particles for w in self.workloads)
+        return f"{len(self.workloads)}inst-{tri}tri-{par}p"
 
     def read_species(self, sid):
         k, _, n = self.species[sid]

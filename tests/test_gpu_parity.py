@@ -204,6 +204,50 @@ def test_deterministic_rerun(fx, precision):
             assert np.array_equal(a[k], b[k]), k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_equals_plain_launches(fx, precision):
+    """Steps replayed from captured CUDA graphs (all pushers' graphs, both particle-buffer parities,
+    sorting and non-sorting steps) give bit-identical results to plain launches."""
+    fetdpic, _ = fx
+    w = inputs.pair_plasma(12, 5, kT=0.2, seed=17, pusher="boris")
+    outs = []
+    for graphs in (False, True):
+        s = fetdpic.Simulation(w, precision=precision, spai_level=1, sort_interval=3, use_graphs=graphs).load()
+        s.step(5, "boris").step(4, "vay").step(7, "hc").sync()
+        outs.append((s.read_fields(), s.read_species(0), s.read_species(1)))
+        s.close()
+    for a, b in zip(outs[0], outs[1]):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotune_leaves_state_unchanged(fx, precision, tmp_path):
+    """The autotuner's trials start from and restore the current state: a tuned run equals an
+    untuned run configured with the same choice, bit for bit; the cache reproduces the choice."""
+    fetdpic, _ = fx
+    w = inputs.pair_plasma(16, 6, kT=0.2, seed=19, pusher="vay")
+    a = fetdpic.Simulation(w, precision=precision, spai_level=1).load()
+    a.step(3, "vay")
+    cache = str(tmp_path / "tune.json")
+    v, s = a.autotune("vay", trial_steps=16, cache=cache)
+    assert v in (2, 3, 4) and s in (8, 16, 32)
+    a.step(20, "vay").sync()
+    b = fetdpic.Simulation(w, precision=precision, spai_level=1).load()
+    b.step(3, "vay")
+    assert b.autotune("vay", cache=cache) == (v, s)        # served from the cache
+    b.step(20, "vay").sync()
+    for sid in range(2):
+        ga, gb = a.read_species(sid), b.read_species(sid)
+        for k in ga:
+            assert np.array_equal(ga[k], gb[k]), k
+    fa, fb = a.read_fields(), b.read_fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    a.close()
+    b.close()
+
+
 def test_fp32_single_step_tolerance(fx):
     """FP32 path vs the FP64 oracle after one step from the same state.  Tolerances from FP32
     round-off (eps = 6e-8) amplified by the gather/push chain: momenta 2e-5 relative, positions
