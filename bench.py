@@ -43,9 +43,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pair", choices=["pair", "beam", "batched", "cyclotron"],
+                    help="pair: 200k-triangle pair plasma (default); beam: 1M-triangle high-gamma beam; "
+                         "batched: 64 uneven pair plasmas in one launch; cyclotron: 64 electrons")
     ap.add_argument("--side", type=int, default=317, help="jittered grid side (about 2 side^2 triangles)")
     ap.add_argument("--ppc", type=int, default=20, help="particles per species per triangle")
-    ap.add_argument("--pusher", default="vay")
+    ap.add_argument("--pusher", default=None)
     ap.add_argument("--sort-interval", type=int, default=16)
     ap.add_argument("--fp64-steps", type=int, default=0, help="0 = min(steps, 100)")
     ap.add_argument("--e2e-steps", type=int, default=0, help="0 = min(steps, 10)")
@@ -55,17 +58,40 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=1_000_000)
     ap.add_argument("--variant", type=int, default=0, help="FP32 particle-kernel variant (0 = autotuned)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library defaults instead of autotuning")
-    return ap.parse_args()
+    a = ap.parse_args()
+    a.pusher_given = a.pusher is not None
+    if a.pusher is None:
+        a.pusher = "vay"
+    return a
 
 
 def workload(args):
+    """The seeded workload(s): a list of instances (one for all but the batched form)."""
     from paper_1707_04333_gb300 import inputs
-    return inputs.pair_plasma(args.side, args.ppc, kT=0.1, wc_over_wp=0.5, seed=2, pusher=args.pusher)
+    if args.workload == "beam":
+        if not args.pusher_given:
+            args.pusher = "hc"
+        return [inputs.high_gamma_beam(707, 50_000_000, seed=4, pusher=args.pusher)]
+    if args.workload == "batched":
+        return inputs.batched_pair_plasmas(n_inst=64, seed=5)
+    if args.workload == "cyclotron":
+        args.pusher = args.pusher if args.pusher_given else "boris"
+        return [inputs.cyclotron(gamma=2.0, n=64, nx=32, seed=1, pusher=args.pusher)]
+    return [inputs.pair_plasma(args.side, args.ppc, kT=0.1, wc_over_wp=0.5, seed=2, pusher=args.pusher)]
 
 
-def describe(w, args, precision):
-    nf = len(w.mesh.triangles)
-    return (f"pair-plasma {nf} triangles, {w.n_particles} particles (e+p, {args.ppc}/species/triangle), "
+def describe(ws, args, precision):
+    nf = sum(len(w.mesh.triangles) for w in ws)
+    npart = sum(w.n_particles for w in ws)
+    if args.workload == "beam":
+        return (f"high-gamma beam {nf} triangles, {npart} electrons, gamma log-uniform [10, 1000], "
+                f"E_x = 0.5 c B_z, {args.pusher}, {precision}")
+    if args.workload == "batched":
+        return (f"batched pair plasmas: {len(ws)} instances, {nf} triangles, {npart} particles in one launch "
+                f"per stage, {args.pusher}, {precision}")
+    if args.workload == "cyclotron":
+        return f"cyclotron {nf} triangles, {npart} electrons, gamma 2, B_z 1 T, {args.pusher}, {precision}, graphs"
+    return (f"pair-plasma {nf} triangles, {npart} particles (e+p, {args.ppc}/species/triangle), "
             f"{args.pusher}, {precision}")
 
 
@@ -129,7 +155,7 @@ def cpu_oracle(w, sample, steps, warmup=0, seed=5, target_s=None):
     from paper_1707_04333_gb300 import inputs
     oracle.build()
     sim = oracle.OracleSim(w.mesh.nodes, w.mesh.triangles, w.dt, eps0=inputs.EPS0, mu0=inputs.MU0,
-                           c=inputs.C_LIGHT, spai_level=2, b0=w.b0)
+                           c=inputs.C_LIGHT, spai_level=2, b0=w.b0, e0=w.e0, ext=w.ext)
     rng = np.random.default_rng(seed)
     n = 0
     per = max(1, sample // len(w.species))
@@ -154,14 +180,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = workload(args)
+    ws = workload(args)
+    w = max(ws, key=lambda x: x.n_particles)
     sample = 250_000
     val, n, dt, _ = cpu_oracle(w, sample, args.steps, warmup=args.warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": describe(w, args, "fp64 CPU oracle"),
+        "data": "synthetic", "config": {"workload": describe(ws, args, "fp64 CPU oracle"),
                                         "sample_particles": n},
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{n} of {w.n_particles} particles, full mesh and field update, "
@@ -196,12 +223,16 @@ def main():
     barrier()
     build_lib.build()
 
-    w = workload(args)
+    ws = workload(args)
+    w = max(ws, key=lambda x: x.n_particles)     # the instance the CPU baseline samples
     stream = torch.cuda.Stream()          # explicit stream: the context's kernels and the timing events
 
-    def timed_run(precision, steps, warmup, stages=True):
-        sim = fetdpic.Simulation(w, precision=precision, spai_level=2, sort_interval=args.sort_interval,
-                                 time_stages=stages, stream=stream, kernel_variant=args.variant)
+    graphs = args.workload == "cyclotron"        # launch-bound: replay captured graphs, no stage events
+
+    def timed_run(precision, steps, warmup, stages=not graphs):
+        sim = fetdpic.Simulation(ws, precision=precision, spai_level=2, sort_interval=args.sort_interval,
+                                 time_stages=stages, stream=stream, kernel_variant=args.variant,
+                                 use_graphs=graphs)
         sim.load()
         if args.variant == 0 and not args.no_tune:
             tuned = sim.autotune(args.pusher, trial_steps=32,
@@ -245,7 +276,7 @@ def main():
         ms = float(t.item())
     K = args.steps
     value = npart * K * world / (ms / 1e3)
-    part_ms = st[1] / max(st[3], 1)
+    part_ms = st[1] / max(st[3], 1) if st[3] > 0 else 0.0
     peak, peak_kind = peaks()
     achieved = pbytes / (part_ms / 1e3) / 1e9 if part_ms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -314,7 +345,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, dt, ns = cpu_oracle(w, args.cpu_sample, 0, target_s=15.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} of {w.n_particles} particles (seeded), full {len(w.mesh.triangles)}-triangle mesh "
+               "sample": f"{n} of {w.n_particles} particles (seeded) of the largest instance, full "
+                         f"{len(w.mesh.triangles)}-triangle mesh "
                          f"and field update, {ns} steps, {dt:.1f} s"}
 
     if rank == 0:
@@ -322,9 +354,10 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": describe(w, args, "fp32 cell-local barycentric"),
+            "config": {"workload": describe(ws, args, "fp32 cell-local barycentric"),
                        "tuning": {"kernel_variant": sim_tuned[0], "sort_interval": sim_tuned[1]},
-                       "triangles": len(w.mesh.triangles), "particles_per_gpu": npart,
+                       "triangles": sum(len(x.mesh.triangles) for x in ws), "particles_per_gpu": npart,
+                       "instances": len(ws),
                        "l2": "inputs larger than L2 (particle state 2 x 161 MB per step)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,

@@ -8,7 +8,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/fetdpic.h"
+#include "fetdpic.h"
 
 namespace fetdpic {
 

@@ -291,146 +291,125 @@ constexpr int P32_BLOCK = 256;
 constexpr int P32_WARPS = P32_BLOCK / 32;
 constexpr int P32_QUEUE = 64;                // walker ring per warp
 
-// Persistent kernel: each warp takes a contiguous range of 32-particle chunks,
-// with the next chunk's particle state loaded into registers while the
-// current one is processed.  Species ranges are padded to 1024, so a chunk
-// never straddles species.  Loads per particle: 20 B of state (coalesced), the
-// triangle constants (64 B) and field record (32 B), shared by the sorted
-// particles of one triangle.  The first sub-segment's current is reduced in
-// 32-bit fixed point over runs of equal triangle across the warp (segmented
-// shuffle scan); the run head widens to 64 bits and adds three integers with
-// atomics.  Particles whose path leaves their triangle (about one in ten) go
-// to the warp's ring in shared memory and are walked 32 at a time, so the
-// divergent walk runs with full warps and the common path only tests that the
-// end point is inside.  Integer sums are exact: the result
-// does not depend on particle, queue or atomic order.
-template <int PUSHER, int MINB>
-__global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
+// Particle state of one lane's particle and the records of its triangle.
+struct PState { int f, sp; float l0, l1, ux, uy; };
+struct PRec { float4 c0, c1, r0, r1; };
+
+__device__ __forceinline__ PState load_state(const StepArgs32 &a, unsigned c, int lane)
 {
-    __shared__ WalkItem qbuf[P32_WARPS][P32_QUEUE];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    WalkItem *q = qbuf[warp];
-    unsigned qhead = 0, qtail = 0;                    // warp-uniform ring positions
-    // warp w takes the contiguous chunks [w K, (w+1) K): consecutive chunks of
-    // sorted particles share triangles, so their records come from L1
-    const long long nwarps = (long long)gridDim.x * P32_WARPS;
-    const long long wid = (long long)blockIdx.x * P32_WARPS + warp;
-    const long long K = (a.nchunks + nwarps - 1) / nwarps;
-    long long c = wid * K;
-    const long long cend = min(c + K, a.nchunks);
+    const unsigned p = c * 32u + (unsigned)lane;
+    PState s;
+    s.f = a.cell[p]; s.l0 = a.l0[p]; s.l1 = a.l1[p]; s.ux = a.ux[p]; s.uy = a.uy[p];
+    s.sp = a.chunk_sp[c];
+    return s;
+}
+
+__device__ __forceinline__ PRec load_rec(const StepArgs32 &a, int f)
+{
+    PRec r;
+    if (f >= 0) {
+        const float4 *cp = reinterpret_cast<const float4 *>(a.cst + f);
+        const float4 *rp = reinterpret_cast<const float4 *>(a.rec + f);
+        r.c0 = cp[0]; r.c1 = cp[1]; r.r0 = rp[0]; r.r1 = rp[1];
+    } else {
+        r.c0 = r.c1 = r.r0 = r.r1 = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return r;
+}
+
+// One 32-particle chunk: gather, push, in-triangle test, current of the
+// particles that stay (warp-segmented 32-bit reduction + integer atomics by
+// the run heads), state stores; walkers go to the warp's ring, which is walked
+// 32 at a time.
+template <int PUSHER>
+__device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, int lane, const PState &s,
+                                              const PRec &r, WalkItem *q, unsigned &qhead, unsigned &qtail)
+{
     const unsigned full = 0xffffffffu;
-
-    int fn = -1;
-    float l0n = 0.f, l1n = 0.f, uxn = 0.f, uyn = 0.f;
-    if (c < cend) {
-        const long long pn = c * 32 + lane;
-        fn = a.cell[pn]; l0n = a.l0[pn]; l1n = a.l1[pn]; uxn = a.ux[pn]; uyn = a.uy[pn];
+    const unsigned p = c * 32u + (unsigned)lane;
+    const Sp32 *spp = a.sp + s.sp;
+    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
+    const float wfix = __ldg(&spp->wfix);
+    const bool live = s.f >= 0;
+    int v0[3] = {0, 0, 0};
+    int key = -1;
+    bool walking = false;
+    float ux = s.ux, uy = s.uy;
+    float lf0 = 0.f, lf1 = 0.f;
+    WalkItem it;
+    if (live) {
+        const float l0 = s.l0, l1 = s.l1;
+        const float l2 = 1.f - l0 - l1;
+        // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
+        const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
+        const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
+        const float bz = s0.x * r.r1.z + s0.w;
+        // push (Sec. II.C); FP64 when gamma > 10
+        float ig, vx, vy;
+        if (1.f + ux * ux + uy * uy > 100.f) {
+            const PushOut o = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
+            ux = o.ux; uy = o.uy; vx = o.vx; vy = o.vy; ig = o.ig;
+        } else {
+            ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
+            vx = ux * ig; vy = uy * ig;
+        }
+        if (!isfinite(vx + vy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+        // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
+        const float g0 = r.c0.x * vx + r.c0.y * vy;
+        const float g1 = r.c0.z * vx + r.c0.w * vy;
+        const float g2 = r.c1.x * vx + r.c1.y * vy;
+        lf0 = l0 + g0;
+        lf1 = l1 + g1;
+        if (lf0 >= 0.f && lf1 >= 0.f && l2 + g2 >= 0.f) {
+            // stays in its triangle: i_ab += (Q/dt)(l_a^s dl_b - dl_a l_b^s), Eq. (I.assign)
+            key = s.f;
+            v0[0] = __float2int_rn((l1 * g2 - g1 * l2) * wfix);
+            v0[1] = __float2int_rn((l2 * g0 - g2 * l0) * wfix);
+            v0[2] = __float2int_rn((l0 * g1 - g0 * l1) * wfix);
+        } else {
+            walking = true;
+            it.p = p; it.f = s.f; it.sp = s.sp;
+            it.l0 = l0; it.l1 = l1; it.l2 = l2; it.pad = 0.f;
+            it.ux = ux; it.uy = uy; it.vx = vx; it.vy = vy;
+        }
     }
-    for (; c < cend; ++c) {
-        const long long p = c * 32 + lane;
-        const int f = fn;
-        const float l0 = l0n, l1 = l1n;
-        float ux = uxn, uy = uyn;
-        const long long cn = c + 1;
-        if (cn < cend) {
-            const long long pn = cn * 32 + lane;
-            fn = a.cell[pn]; l0n = a.l0[pn]; l1n = a.l1[pn]; uxn = a.ux[pn]; uyn = a.uy[pn];
-        }
-        const int spid = a.chunk_sp[c];
-        const Sp32 *spp = a.sp + spid;
-        const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
-        const float wfix = __ldg(&spp->wfix);
-        const bool live = f >= 0;
-
-        int v0[3] = {0, 0, 0};
-        int ew0[3] = {0, 0, 0};
-        int key = -1;
-        bool walking = false;
-        float lfin[3] = {0.f, 0.f, 0.f};
-        WalkItem it;
-        if (live) {
-            const float4 *cp = reinterpret_cast<const float4 *>(a.cst + f);
-            const float4 c0 = cp[0], c1 = cp[1];
-            const float4 *rp = reinterpret_cast<const float4 *>(a.rec + f);
-            const float4 r0 = rp[0], r1 = rp[1];
-            ew0[0] = __float_as_int(r1.w); ew0[1] = __float_as_int(c1.z); ew0[2] = __float_as_int(c1.w);
-            const float l2 = 1.f - l0 - l1;
-            // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
-            const float ex = s0.x * (l0 * r0.x + l1 * r0.z + l2 * r1.x) + s0.y;
-            const float ey = s0.x * (l0 * r0.y + l1 * r0.w + l2 * r1.y) + s0.z;
-            const float bz = s0.x * r1.z + s0.w;
-            // push (Sec. II.C); FP64 when gamma > 10
-            float ig, vx, vy;
-            if (1.f + ux * ux + uy * uy > 100.f) {
-                const PushOut o = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
-                ux = o.ux; uy = o.uy; vx = o.vx; vy = o.vy; ig = o.ig;
-            } else {
-                ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
-                vx = ux * ig; vy = uy * ig;
-            }
-            if (!isfinite(ux + uy + ig)) atomicOr(a.status, (unsigned)ST_NONFINITE);
-            // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
-            const float g0 = c0.x * vx + c0.y * vy;
-            const float g1 = c0.z * vx + c0.w * vy;
-            const float g2 = c1.x * vx + c1.y * vy;
-            lfin[0] = l0 + g0;
-            lfin[1] = l1 + g1;
-            lfin[2] = l2 + g2;
-            if (lfin[0] >= 0.f && lfin[1] >= 0.f && lfin[2] >= 0.f) {
-                // stays in its triangle: i_ab += (Q/dt)(l_a^s dl_b - dl_a l_b^s), Eq. (I.assign)
-                // with l^f = l^s + dl
-                key = f;
-                lfin[2] = 1.f - lfin[0] - lfin[1];
-                v0[0] = __float2int_rn((l1 * g2 - g1 * l2) * wfix);
-                v0[1] = __float2int_rn((l2 * g0 - g2 * l0) * wfix);
-                v0[2] = __float2int_rn((l0 * g1 - g0 * l1) * wfix);
-            } else {
-                walking = true;
-                it.p = p; it.f = f; it.sp = spid;
-                it.l0 = l0; it.l1 = l1; it.l2 = l2; it.pad = 0.f;
-                it.ux = ux; it.uy = uy; it.vx = vx; it.vy = vy;
-            }
-        }
-        // queue the walkers of this chunk
-        const unsigned wm = __ballot_sync(full, walking);
-        if (walking) {
-            const unsigned rank = __popc(wm & ((1u << lane) - 1u));
-            q[(qtail + rank) & (P32_QUEUE - 1)] = it;
-        }
-        qtail += __popc(wm);
-
-        // warp segmented reduction of the first sub-segment over runs of equal triangle
-        {
-            const int kn = __shfl_down_sync(full, key, 1);
-            const bool tail = (lane == 31) || (kn != key);
-            const unsigned tails = __ballot_sync(full, tail);
-            const int seg_end = lane + __ffs(tails >> lane) - 1;
-            const int kp = __shfl_up_sync(full, key, 1);
-            const bool head = (lane == 0) || (kp != key);
+    const unsigned wm = __ballot_sync(full, walking);
+    if (walking) q[(qtail + __popc(wm & ((1u << lane) - 1u))) & (P32_QUEUE - 1)] = it;
+    qtail += __popc(wm);
+    {
+        const int kn = __shfl_down_sync(full, key, 1);
+        const unsigned tails = __ballot_sync(full, (lane == 31) || (kn != key));
+        const int seg_end = lane + __ffs(tails >> lane) - 1;
+        const int kp = __shfl_up_sync(full, key, 1);
+        const bool head = (lane == 0) || (kp != key);
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int o0 = __shfl_down_sync(full, v0[0], off);
-                const int o1 = __shfl_down_sync(full, v0[1], off);
-                const int o2 = __shfl_down_sync(full, v0[2], off);
-                if (lane + off <= seg_end) { v0[0] += o0; v0[1] += o1; v0[2] += o2; }
-            }
-            if (head && key >= 0) add_seg32(a.ifix, ew0, v0);
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o0 = __shfl_down_sync(full, v0[0], off);
+            const int o1 = __shfl_down_sync(full, v0[1], off);
+            const int o2 = __shfl_down_sync(full, v0[2], off);
+            if (lane + off <= seg_end) { v0[0] += o0; v0[1] += o1; v0[2] += o2; }
         }
-        if (live && !walking) {
-            a.l0[p] = lfin[0]; a.l1[p] = lfin[1];
-            a.ux[p] = ux; a.uy[p] = uy;
-            if (a.rec_cap > 0) a.rec_cnt[p] = 0;
-        }
-        // walk on 32 queued particles at once
-        if (qtail - qhead >= 32) {
-            __syncwarp();
-            const WalkItem w = q[(qhead + lane) & (P32_QUEUE - 1)];
-            walk_particle(a, w);
-            qhead += 32;
-            __syncwarp();
+        if (head && key >= 0) {
+            const int ew[3] = {__float_as_int(r.r1.w), __float_as_int(r.c1.z), __float_as_int(r.c1.w)};
+            add_seg32(a.ifix, ew, v0);
         }
     }
-    // drain
+    if (live && !walking) {
+        a.l0[p] = lf0; a.l1[p] = lf1;
+        a.ux[p] = ux; a.uy[p] = uy;
+        if (a.rec_cap > 0) a.rec_cnt[p] = 0;
+    }
+    if (qtail - qhead >= 32) {
+        __syncwarp();
+        const WalkItem w = q[(qhead + lane) & (P32_QUEUE - 1)];
+        walk_particle(a, w);
+        qhead += 32;
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void drain(const StepArgs32 &a, WalkItem *q, unsigned qhead, unsigned qtail, int lane)
+{
     const unsigned left = qtail - qhead;
     if (left > 0) {
         __syncwarp();
@@ -439,6 +418,51 @@ __global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
             walk_particle(a, w);
         }
     }
+}
+
+// Persistent kernel: each warp takes a contiguous range of 32-particle chunks
+// (consecutive chunks of sorted particles share triangles, so their records
+// come from L1).  MINB >= 3: the next chunk's particle state is loaded into
+// registers while the current one is processed.  MINB == 2 (half the warps,
+// more registers): particle state two chunks ahead and the next chunk's
+// triangle records one chunk ahead.  Species ranges are padded to 1024, so a
+// chunk never straddles species.  Integer sums are exact: the result does not
+// depend on particle, queue or atomic order.
+template <int PUSHER, int MINB>
+__global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
+{
+    __shared__ WalkItem qbuf[P32_WARPS][P32_QUEUE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkItem *q = qbuf[warp];
+    unsigned qhead = 0, qtail = 0;                    // warp-uniform ring positions
+    const unsigned nwarps = gridDim.x * P32_WARPS;
+    const unsigned wid = blockIdx.x * P32_WARPS + warp;
+    const unsigned K = (unsigned)((a.nchunks + nwarps - 1) / nwarps);
+    unsigned c = wid * K;
+    const unsigned cend = (unsigned)min((long long)c + K, a.nchunks);
+    if (c >= cend) return;
+    if (MINB >= 3) {
+        PState sn = load_state(a, c, lane);
+        for (; c < cend; ++c) {
+            const PState s = sn;
+            if (c + 1 < cend) sn = load_state(a, c + 1, lane);
+            const PRec r = load_rec(a, s.f);
+            process_chunk<PUSHER>(a, c, lane, s, r, q, qhead, qtail);
+        }
+    } else {
+        PState s = load_state(a, c, lane);
+        PState s1 = s, s2 = s;
+        if (c + 1 < cend) s1 = load_state(a, c + 1, lane);
+        PRec r = load_rec(a, s.f);
+        for (; c < cend; ++c) {
+            if (c + 2 < cend) s2 = load_state(a, c + 2, lane);
+            PRec r1 = r;
+            if (c + 1 < cend) r1 = load_rec(a, s1.f);
+            process_chunk<PUSHER>(a, c, lane, s, r, q, qhead, qtail);
+            s = s1; s1 = s2; r = r1;
+        }
+    }
+    drain(a, q, qhead, qtail, lane);
 }
 
 // Persistent grid: resident blocks per SM (from the occupancy calculator) times

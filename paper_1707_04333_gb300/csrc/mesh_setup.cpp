@@ -12,7 +12,7 @@
 #include <unordered_map>
 
 #include "fetdpic_internal.h"
-#include "../../include/fetdpic.h"
+#include "fetdpic.h"
 
 namespace fetdpic {
 
