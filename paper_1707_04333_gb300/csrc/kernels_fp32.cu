@@ -306,14 +306,12 @@ __device__ __forceinline__ PState load_state(const StepArgs32 &a, unsigned c, in
 
 __device__ __forceinline__ PRec load_rec(const StepArgs32 &a, int f)
 {
+    // padding slots (f < 0) read triangle 0; their results are discarded
+    const int g = f < 0 ? 0 : f;
+    const float4 *cp = reinterpret_cast<const float4 *>(a.cst + g);
+    const float4 *rp = reinterpret_cast<const float4 *>(a.rec + g);
     PRec r;
-    if (f >= 0) {
-        const float4 *cp = reinterpret_cast<const float4 *>(a.cst + f);
-        const float4 *rp = reinterpret_cast<const float4 *>(a.rec + f);
-        r.c0 = cp[0]; r.c1 = cp[1]; r.r0 = rp[0]; r.r1 = rp[1];
-    } else {
-        r.c0 = r.c1 = r.r0 = r.r1 = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    r.c0 = cp[0]; r.c1 = cp[1]; r.r0 = rp[0]; r.r1 = rp[1];
     return r;
 }
 
@@ -331,47 +329,43 @@ __device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, i
     const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
     const float wfix = __ldg(&spp->wfix);
     const bool live = s.f >= 0;
-    int v0[3] = {0, 0, 0};
-    int key = -1;
-    bool walking = false;
+    int v0[3];
     float ux = s.ux, uy = s.uy;
-    float lf0 = 0.f, lf1 = 0.f;
     WalkItem it;
-    if (live) {
-        const float l0 = s.l0, l1 = s.l1;
-        const float l2 = 1.f - l0 - l1;
-        // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
-        const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
-        const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
-        const float bz = s0.x * r.r1.z + s0.w;
-        // push (Sec. II.C); FP64 when gamma > 10
-        float ig, vx, vy;
-        if (1.f + ux * ux + uy * uy > 100.f) {
-            const PushOut o = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
-            ux = o.ux; uy = o.uy; vx = o.vx; vy = o.vy; ig = o.ig;
-        } else {
-            ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
-            vx = ux * ig; vy = uy * ig;
-        }
-        if (!isfinite(vx + vy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
-        // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
-        const float g0 = r.c0.x * vx + r.c0.y * vy;
-        const float g1 = r.c0.z * vx + r.c0.w * vy;
-        const float g2 = r.c1.x * vx + r.c1.y * vy;
-        lf0 = l0 + g0;
-        lf1 = l1 + g1;
-        if (lf0 >= 0.f && lf1 >= 0.f && l2 + g2 >= 0.f) {
-            // stays in its triangle: i_ab += (Q/dt)(l_a^s dl_b - dl_a l_b^s), Eq. (I.assign)
-            key = s.f;
-            v0[0] = __float2int_rn((l1 * g2 - g1 * l2) * wfix);
-            v0[1] = __float2int_rn((l2 * g0 - g2 * l0) * wfix);
-            v0[2] = __float2int_rn((l0 * g1 - g0 * l1) * wfix);
-        } else {
-            walking = true;
-            it.p = p; it.f = s.f; it.sp = s.sp;
-            it.l0 = l0; it.l1 = l1; it.l2 = l2; it.pad = 0.f;
-            it.ux = ux; it.uy = uy; it.vx = vx; it.vy = vy;
-        }
+    // straight-line for every lane (padding lanes compute on triangle 0 and are masked below)
+    const float l0 = s.l0, l1 = s.l1;
+    const float l2 = 1.f - l0 - l1;
+    // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
+    const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
+    const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
+    const float bz = s0.x * r.r1.z + s0.w;
+    // push (Sec. II.C); FP64 when gamma > 10
+    float ig, vx, vy;
+    if (1.f + ux * ux + uy * uy > 100.f) {
+        const PushOut o = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
+        ux = o.ux; uy = o.uy; vx = o.vx; vy = o.vy; ig = o.ig;
+    } else {
+        ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
+        vx = ux * ig; vy = uy * ig;
+    }
+    if (live && !isfinite(vx + vy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
+    const float g0 = r.c0.x * vx + r.c0.y * vy;
+    const float g1 = r.c0.z * vx + r.c0.w * vy;
+    const float g2 = r.c1.x * vx + r.c1.y * vy;
+    const float lf0 = l0 + g0, lf1 = l1 + g1;
+    const bool stays = lf0 >= 0.f && lf1 >= 0.f && l2 + g2 >= 0.f;
+    const bool walking = live && !stays;
+    const int key = (live && stays) ? s.f : -1;
+    // stays in its triangle: i_ab += (Q/dt)(l_a^s dl_b - dl_a l_b^s), Eq. (I.assign)
+    const float wk = (live && stays) ? wfix : 0.f;
+    v0[0] = __float2int_rn((l1 * g2 - g1 * l2) * wk);
+    v0[1] = __float2int_rn((l2 * g0 - g2 * l0) * wk);
+    v0[2] = __float2int_rn((l0 * g1 - g0 * l1) * wk);
+    if (walking) {
+        it.p = p; it.f = s.f; it.sp = s.sp;
+        it.l0 = l0; it.l1 = l1; it.l2 = l2; it.pad = 0.f;
+        it.ux = ux; it.uy = uy; it.vx = vx; it.vy = vy;
     }
     const unsigned wm = __ballot_sync(full, walking);
     if (walking) q[(qtail + __popc(wm & ((1u << lane) - 1u))) & (P32_QUEUE - 1)] = it;
@@ -394,7 +388,7 @@ __device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, i
             add_seg32(a.ifix, ew, v0);
         }
     }
-    if (live && !walking) {
+    if (live && stays) {
         a.l0[p] = lf0; a.l1[p] = lf1;
         a.ux[p] = ux; a.uy[p] = uy;
         if (a.rec_cap > 0) a.rec_cnt[p] = 0;
