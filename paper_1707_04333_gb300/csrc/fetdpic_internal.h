@@ -107,7 +107,7 @@ struct Species {
 };
 
 enum StatusBits : unsigned {
-    ST_WALK = 1u, ST_NONFINITE = 2u, ST_MESH = 4u
+    ST_WALK = 1u, ST_NONFINITE = 2u, ST_MESH = 4u, ST_TIMEOUT = 8u
 };
 
 // ----------------------------------------------------------- launchers

@@ -299,8 +299,10 @@ __device__ __forceinline__ PState load_state(const StepArgs32 &a, unsigned c, in
 {
     const unsigned p = c * 32u + (unsigned)lane;
     PState s;
-    s.f = a.cell[p]; s.l0 = a.l0[p]; s.l1 = a.l1[p]; s.ux = a.ux[p]; s.uy = a.uy[p];
-    s.sp = a.chunk_sp[c];
+    // streamed once per step: evict-first, so L1 keeps the triangle records
+    s.f = __ldcs(a.cell + p); s.l0 = __ldcs(a.l0 + p); s.l1 = __ldcs(a.l1 + p);
+    s.ux = __ldcs(a.ux + p); s.uy = __ldcs(a.uy + p);
+    s.sp = __ldg(a.chunk_sp + c);
     return s;
 }
 
@@ -311,7 +313,7 @@ __device__ __forceinline__ PRec load_rec(const StepArgs32 &a, int f)
     const float4 *cp = reinterpret_cast<const float4 *>(a.cst + g);
     const float4 *rp = reinterpret_cast<const float4 *>(a.rec + g);
     PRec r;
-    r.c0 = cp[0]; r.c1 = cp[1]; r.r0 = rp[0]; r.r1 = rp[1];
+    r.c0 = __ldg(cp); r.c1 = __ldg(cp + 1); r.r0 = __ldg(rp); r.r1 = __ldg(rp + 1);
     return r;
 }
 
@@ -389,8 +391,8 @@ __device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, i
         }
     }
     if (live && stays) {
-        a.l0[p] = lf0; a.l1[p] = lf1;
-        a.ux[p] = ux; a.uy[p] = uy;
+        __stcs(a.l0 + p, lf0); __stcs(a.l1 + p, lf1);
+        __stcs(a.ux + p, ux); __stcs(a.uy + p, uy);
         if (a.rec_cap > 0) a.rec_cnt[p] = 0;
     }
     if (qtail - qhead >= 32) {
@@ -416,12 +418,11 @@ __device__ __forceinline__ void drain(const StepArgs32 &a, WalkItem *q, unsigned
 
 // Persistent kernel: each warp takes a contiguous range of 32-particle chunks
 // (consecutive chunks of sorted particles share triangles, so their records
-// come from L1).  MINB >= 3: the next chunk's particle state is loaded into
-// registers while the current one is processed.  MINB == 2 (half the warps,
-// more registers): particle state two chunks ahead and the next chunk's
-// triangle records one chunk ahead.  Species ranges are padded to 1024, so a
-// chunk never straddles species.  Integer sums are exact: the result does not
-// depend on particle, queue or atomic order.
+// come from L1); the next chunk's particle state is loaded into registers
+// while the current one is processed.  MINB only sets the register budget.
+// Species ranges are padded to 1024, so a chunk never straddles species.
+// Integer sums are exact and every variant runs the same per-particle code,
+// so the result depends on neither MINB nor particle, queue or atomic order.
 template <int PUSHER, int MINB>
 __global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
 {
@@ -435,26 +436,135 @@ __global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
     unsigned c = wid * K;
     const unsigned cend = (unsigned)min((long long)c + K, a.nchunks);
     if (c >= cend) return;
-    if (MINB >= 3) {
-        PState sn = load_state(a, c, lane);
-        for (; c < cend; ++c) {
-            const PState s = sn;
-            if (c + 1 < cend) sn = load_state(a, c + 1, lane);
-            const PRec r = load_rec(a, s.f);
-            process_chunk<PUSHER>(a, c, lane, s, r, q, qhead, qtail);
-        }
-    } else {
-        PState s = load_state(a, c, lane);
-        PState s1 = s, s2 = s;
-        if (c + 1 < cend) s1 = load_state(a, c + 1, lane);
-        PRec r = load_rec(a, s.f);
-        for (; c < cend; ++c) {
-            if (c + 2 < cend) s2 = load_state(a, c + 2, lane);
-            PRec r1 = r;
-            if (c + 1 < cend) r1 = load_rec(a, s1.f);
-            process_chunk<PUSHER>(a, c, lane, s, r, q, qhead, qtail);
-            s = s1; s1 = s2; r = r1;
-        }
+    PState sn = load_state(a, c, lane);
+    for (; c < cend; ++c) {
+        const PState s = sn;
+        if (c + 1 < cend) sn = load_state(a, c + 1, lane);
+        const PRec r = load_rec(a, s.f);
+        process_chunk<PUSHER>(a, c, lane, s, r, q, qhead, qtail);
+    }
+    drain(a, q, qhead, qtail, lane);
+}
+
+// ------------------------------------------------------- staged variant
+// Particle state streamed into shared memory by bulk asynchronous copies
+// (cp.async.bulk, completion on an mbarrier), ST_DEPTH chunks ahead of the
+// chunk being processed: one lane per warp issues five 128-byte copies per
+// chunk (cell, l0, l1, ux, uy), so the bytes in flight no longer depend on the
+// registers a thread can spare.  Every wait on an mbarrier is bounded; a wait
+// that gives up sets ST_TIMEOUT and the warp stops after draining its copies.
+constexpr int ST_DEPTH = 4;
+constexpr unsigned ST_SPIN = 1u << 20;
+
+struct __align__(16) StageBuf {
+    int cell[32];
+    float l0[32], l1[32], ux[32], uy[32];
+};
+
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`; false after ST_SPIN polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (unsigned k = 0; k < ST_SPIN; ++k)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// Lane 0 of the warp: start the copies of chunk c into stage buffer `b`.
+__device__ __forceinline__ void stage_issue(const StepArgs32 &a, unsigned c, StageBuf *b, unsigned long long *bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");     // earlier reads of this buffer first
+    mbar_expect_tx(bar, 5 * 128);
+    const size_t o = (size_t)c * 32;
+    bulk_to_smem(b->cell, a.cell + o, 128, bar);
+    bulk_to_smem(b->l0, a.l0 + o, 128, bar);
+    bulk_to_smem(b->l1, a.l1 + o, 128, bar);
+    bulk_to_smem(b->ux, a.ux + o, 128, bar);
+    bulk_to_smem(b->uy, a.uy + o, 128, bar);
+}
+
+template <int PUSHER>
+__global__ void __launch_bounds__(P32_BLOCK, 3) k_particles32_staged(StepArgs32 a)
+{
+    __shared__ WalkItem qbuf[P32_WARPS][P32_QUEUE];
+    __shared__ StageBuf sbuf[P32_WARPS][ST_DEPTH];
+    __shared__ unsigned long long sbar[P32_WARPS][ST_DEPTH];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkItem *q = qbuf[warp];
+    StageBuf *buf = sbuf[warp];
+    unsigned long long *bar = sbar[warp];
+    unsigned qhead = 0, qtail = 0;
+    const unsigned nwarps = gridDim.x * P32_WARPS;
+    const unsigned wid = blockIdx.x * P32_WARPS + warp;
+    const unsigned K = (unsigned)((a.nchunks + nwarps - 1) / nwarps);
+    const unsigned c0 = wid * K;
+    const unsigned cend = (unsigned)min((long long)c0 + K, a.nchunks);
+    if (c0 >= cend) return;
+    if (lane == 0) {
+        for (int s = 0; s < ST_DEPTH; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int s = 0; s < ST_DEPTH; ++s)
+            if (c0 + s < cend) stage_issue(a, c0 + s, &buf[s], &bar[s]);
+    __syncwarp();
+    unsigned phase = 0;                               // bit s = parity to wait for on stage s
+    int spn = a.chunk_sp[c0];
+    bool ok = true;
+    for (unsigned c = c0; c < cend; ++c) {
+        const int s = (int)((c - c0) % ST_DEPTH);
+        const int sp = spn;
+        if (c + 1 < cend) spn = a.chunk_sp[c + 1];
+        // all lanes poll; the warp gives up together so no lane is left in a full-mask shuffle
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[s], (phase >> s) & 1u))) { ok = false; break; }
+        phase ^= 1u << s;
+        PState st;
+        st.f = buf[s].cell[lane]; st.l0 = buf[s].l0[lane]; st.l1 = buf[s].l1[lane];
+        st.ux = buf[s].ux[lane]; st.uy = buf[s].uy[lane]; st.sp = sp;
+        __syncwarp();
+        if (lane == 0 && c + ST_DEPTH < cend) stage_issue(a, c + ST_DEPTH, &buf[s], &bar[s]);
+        const PRec r = load_rec(a, st.f);
+        process_chunk<PUSHER>(a, c, lane, st, r, q, qhead, qtail);
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
+        // let the copies still in flight land before the block's shared memory goes away
+        for (int s = 0; s < ST_DEPTH; ++s) mbar_wait(&bar[s], (phase >> s) & 1u);
+        return;
     }
     drain(a, q, qhead, qtail, lane);
 }
@@ -481,9 +591,28 @@ static void launch_p32(cudaStream_t st, const StepArgs32 &a)
 }
 
 template <int PUSHER>
+static void launch_p32s(cudaStream_t st, const StepArgs32 &a)
+{
+    static int per_sm = 0, sms = 0, dev = -1;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev || per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32_staged<PUSHER>, P32_BLOCK, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        dev = d;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long need = (a.nchunks + P32_WARPS - 1) / P32_WARPS;
+    const long long grid = std::min<long long>(need, (long long)per_sm * sms);
+    if (grid <= 0) return;
+    k_particles32_staged<PUSHER><<<(unsigned)grid, P32_BLOCK, 0, st>>>(a);
+}
+
+template <int PUSHER>
 static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
 {
     switch (a.variant) {
+    case 5: launch_p32s<PUSHER>(st, a); break;
     case 2: launch_p32<PUSHER, 2>(st, a); break;
     case 4: launch_p32<PUSHER, 4>(st, a); break;
     default: launch_p32<PUSHER, 3>(st, a); break;     // measured best on GB300 (no spills, 24 warps/SM)

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import build_lib
 
-OK, EINVAL, ENOMEM, ECUDA, EMESH, EWALK, EOUTSIDE, ENONFINITE, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -9
+OK, EINVAL, ENOMEM, ECUDA, EMESH, EWALK, EOUTSIDE, ENONFINITE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 PUSHERS = {"boris": 0, "boris_tan": 1, "vay": 2, "hc": 3}
 FP64, FP32 = 0, 1
 
