@@ -423,15 +423,15 @@ __device__ __forceinline__ void drain(const StepArgs32 &a, WalkItem *q, unsigned
 // Species ranges are padded to 1024, so a chunk never straddles species.
 // Integer sums are exact and every variant runs the same per-particle code,
 // so the result depends on neither MINB nor particle, queue or atomic order.
-template <int PUSHER, int MINB>
-__global__ void __launch_bounds__(P32_BLOCK, MINB) k_particles32(StepArgs32 a)
+template <int PUSHER, int MINB, int NW>
+__global__ void __launch_bounds__(NW * 32, MINB) k_particles32(StepArgs32 a)
 {
-    __shared__ WalkItem qbuf[P32_WARPS][P32_QUEUE];
+    __shared__ WalkItem qbuf[NW][P32_QUEUE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WalkItem *q = qbuf[warp];
     unsigned qhead = 0, qtail = 0;                    // warp-uniform ring positions
-    const unsigned nwarps = gridDim.x * P32_WARPS;
-    const unsigned wid = blockIdx.x * P32_WARPS + warp;
+    const unsigned nwarps = gridDim.x * NW;
+    const unsigned wid = blockIdx.x * NW + warp;
     const unsigned K = (unsigned)((a.nchunks + nwarps - 1) / nwarps);
     unsigned c = wid * K;
     const unsigned cend = (unsigned)min((long long)c + K, a.nchunks);
@@ -572,22 +572,22 @@ __global__ void __launch_bounds__(P32_BLOCK, 3) k_particles32_staged(StepArgs32 
 // Persistent grid: resident blocks per SM (from the occupancy calculator) times
 // the SM count, capped by the work.  MINB = minimum resident blocks per SM the
 // register allocation targets (2, 3 or 4 x 256 threads); chosen by `variant`.
-template <int PUSHER, int MINB>
+template <int PUSHER, int MINB, int NW = P32_WARPS>
 static void launch_p32(cudaStream_t st, const StepArgs32 &a)
 {
     static int per_sm = 0, sms = 0, dev = -1;
     int d = 0;
     cudaGetDevice(&d);
     if (d != dev || per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32<PUSHER, MINB>, P32_BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32<PUSHER, MINB, NW>, NW * 32, 0);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         dev = d;
         if (per_sm < 1) per_sm = 1;
     }
-    const long long need = (a.nchunks + P32_WARPS - 1) / P32_WARPS;
+    const long long need = (a.nchunks + NW - 1) / NW;
     const long long grid = std::min<long long>(need, (long long)per_sm * sms);
     if (grid <= 0) return;
-    k_particles32<PUSHER, MINB><<<(unsigned)grid, P32_BLOCK, 0, st>>>(a);
+    k_particles32<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
 }
 
 template <int PUSHER>
@@ -613,6 +613,8 @@ static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
 {
     switch (a.variant) {
     case 5: launch_p32s<PUSHER>(st, a); break;
+    case 6: launch_p32<PUSHER, 7, 4>(st, a); break;
+    case 7: launch_p32<PUSHER, 14, 2>(st, a); break;
     case 2: launch_p32<PUSHER, 2>(st, a); break;
     case 4: launch_p32<PUSHER, 4>(st, a); break;
     default: launch_p32<PUSHER, 3>(st, a); break;     // measured best on GB300 (no spills, 24 warps/SM)
