@@ -198,6 +198,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_particles32_pair200k_traffic.json")
+
+
+def measured_traffic(workload, pbytes):
+    """DRAM bytes (read + write) of one particle-kernel launch from the committed ncu summary, or
+    None when the summary is for another workload or the kernel's sources changed since the
+    capture (their SHA-256 is stored with the figure)."""
+    import hashlib
+    try:
+        with open(TRAFFIC_SUMMARY) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None, "no ncu summary"
+    if t.get("workload_flag") != workload or t.get("bytes_per_launch") != pbytes:
+        return None, "ncu summary is for another workload"
+    h = hashlib.sha256()
+    for rel in t["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != t["source_sha256"]:
+        return None, "kernel sources changed since the ncu capture"
+    return t["dram_bytes_per_launch"], f"ncu, one launch (variant {t['variant']}): {os.path.relpath(TRAFFIC_SUMMARY, ROOT)}"
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -279,10 +303,11 @@ def main():
     part_ms = st[1] / max(st[3], 1) if st[3] > 0 else 0.0
     peak, peak_kind = peaks()
     achieved = pbytes / (part_ms / 1e3) / 1e9 if part_ms > 0 else None
+    traffic, traffic_note = measured_traffic(args.workload, pbytes)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": "k_particles32 (gather+push+walk+deposit)", "peak_kind": peak_kind,
-                "bytes_per_launch": pbytes}
+                "bytes_per_launch": pbytes, "traffic_source": traffic_note}
     stages = {"faraday_ms": st[0] / max(st[3], 1), "particles_ms": part_ms,
               "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1)}
 
