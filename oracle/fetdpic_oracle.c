@@ -171,6 +171,30 @@ int ora_locate(const ora_mesh *M, int n, const double *x, const double *y, const
     return bad;
 }
 
+/* Electric field of the edge unknowns at points (Sec. II.B): in the triangle f
+ * holding the point, E = sum_m s_m e_m (l_a grad l_b - l_b grad l_a) with
+ * a = m+1, b = m+2 -- the interpolation of the particle gather, without
+ * external fields.  Used for field probes along a line. */
+void ora_field_at(const ora_mesh *M, const double *e, int n, const int *cell, const double *x, const double *y,
+                  double *exy)
+{
+    for (int p = 0; p < n; ++p) {
+        const int f = cell[p];
+        double lam[3];
+        lambdas(M, f, x[p], y[p], lam);
+        const double *gx = M->gx + 3 * f, *gy = M->gy + 3 * f;
+        double ex = 0.0, ey = 0.0;
+        for (int m = 0; m < 3; ++m) {
+            int a = (m + 1) % 3, b = (m + 2) % 3;
+            double se = M->tri_sign[3 * f + m] * e[M->tri_edge[3 * f + m]];
+            ex += se * (lam[a] * gx[b] - lam[b] * gx[a]);
+            ey += se * (lam[a] * gy[b] - lam[b] * gy[a]);
+        }
+        exy[2 * p] = ex;
+        exy[2 * p + 1] = ey;
+    }
+}
+
 /* ------------------------------------------------------------ Hodge star */
 
 /* Element matrices of [*eps] (Galerkin, eps0 * int W1_m . W1_n dA, Sec. II.A):

@@ -140,6 +140,22 @@ class OracleMesh:
         bad = lib().ora_locate(self.cs, len(x), _p(x), _p(y), None if h is None else _p(h), _p(cell))
         return cell, bad
 
+    def field_at(self, e, x, y, cell=None):
+        """E (n x 2) of the edge unknowns e at points (x, y), by the Whitney 1-form interpolation
+        of the particle gather (Sec. II.B); cell = the triangles holding the points (located
+        here when None)."""
+        x = np.ascontiguousarray(x, np.float64)
+        y = np.ascontiguousarray(y, np.float64)
+        if cell is None:
+            cell, bad = self.locate(x, y)
+            if bad:
+                raise ValueError(f"{bad} points outside the mesh")
+        cell = np.ascontiguousarray(cell, np.int32)
+        e = np.ascontiguousarray(e, np.float64)
+        out = np.zeros((len(x), 2))
+        lib().ora_field_at(self.cs, _p(e), len(x), _p(cell), _p(x), _p(y), _p(out))
+        return out
+
     def hodge_eps(self, eps0: float) -> sp.csr_matrix:
         """[*eps] over all edges (Galerkin edge mass matrix)."""
         el = np.zeros((self.nf, 3, 3))

@@ -123,3 +123,37 @@ def test_spai_level1_pattern(oracle_mod):
     assert (pm - pa).nnz == 0 or ((pm - pa) > 0).nnz == 0
     # symmetric
     assert abs(M - M.T).max() < 1e-12 * abs(M).max()
+
+
+def test_field_at_reproduces_uniform_field(mesh):
+    """Whitney 1-forms span the constant fields: edge unknowns e_ij = E0 . (r_j - r_i) of a uniform
+    E0 give back E0 at any point of any triangle (Sec. II.B), to round-off."""
+    m, om = mesh
+    E0 = np.array([0.37, -1.21])
+    r = m.nodes
+    e = (r[om.edge[:, 1]] - r[om.edge[:, 0]]) @ E0
+    rng = np.random.default_rng(3)
+    pts = inputs.sample_in_triangles(m, np.arange(len(m.triangles)).repeat(3), rng)
+    got = om.field_at(e, pts[:, 0], pts[:, 1])
+    np.testing.assert_allclose(got, np.broadcast_to(E0, got.shape), rtol=0, atol=1e-13)
+
+
+def test_field_at_edge_circulation_and_tangential_continuity(mesh):
+    """For arbitrary edge unknowns, the field's tangential component is constant along each edge and
+    its line integral is the edge unknown (the defining property of the Whitney 1-form basis), so at
+    an edge midpoint E . (r_j - r_i) = e_ij from either neighbouring triangle."""
+    _, om = mesh
+    rng = np.random.default_rng(5)
+    e = rng.normal(size=om.ne)
+    r = np.asarray(om.xy)
+    checked = 0
+    for f in range(om.nf):
+        for k in range(3):
+            g = om.tri_edge[f, k]
+            i, j = om.edge[g]
+            for t in (0.5, 0.2):
+                p = r[i] + t * (r[j] - r[i])
+                E = om.field_at(e, [p[0]], [p[1]], cell=[f])[0]
+                assert abs(E @ (r[j] - r[i]) - e[g]) < 1e-12 * (1 + abs(e[g]))
+                checked += 1
+    assert checked == 6 * om.nf
