@@ -212,6 +212,26 @@ int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *rec);
  * Any output may be NULL. */
 int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double *dgl_max, double *energy);
 
+/* Field probes, a diagnostic around the step: the paper reads its relativistic
+ * Bernstein-mode spectra off E_x sampled along a line of the domain at every
+ * time step, Fourier-transformed in space and time (Sec. III.C).  Registers
+ * n points (inst[n] instance of each point, xy [n][2] in metres; host arrays,
+ * copied).  After every later step the library evaluates E^{n+1} at each point
+ * from the edge unknowns by the Whitney 1-form interpolation of the particle
+ * gather (Sec. II.B: E = sum_m s_m e_m (l_a grad l_b - l_b grad l_a)) and
+ * stores (E_x, E_y) in a device ring holding the last `capacity` steps; no
+ * host transfer per step, and captured step graphs include it.  Replaces any
+ * earlier probes and restarts the record; n = 0 removes them.  Errors: EINVAL
+ * (bad arguments, n > 2^24 or n * capacity > 1e10), EOUTSIDE (a point in no
+ * triangle of its mesh; nothing changes), ENOMEM. */
+int fetdpic_set_probes(fetdpic_ctx *ctx, long long n, const int *inst, const double *xy, long long capacity);
+
+/* Waits for the stream and copies the last min(recorded, capacity, max_rows)
+ * probe rows, oldest first, into exy [rows][n][2] (caller-owned host buffer).
+ * *rows = rows copied, *total = steps recorded since fetdpic_set_probes (either
+ * may be NULL).  ESTATE when no probes are set. */
+int fetdpic_read_probes(fetdpic_ctx *ctx, double *exy, long long max_rows, long long *rows, long long *total);
+
 /* Sizes of instance `inst`: out[0..5] = n_nodes, n_edges, n_tri, n_free_edges,
  * spai nnz, total particles of the instance. */
 int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6]);

@@ -100,6 +100,12 @@ struct fetdpic_ctx {
 
     std::vector<void *> allocs;
 
+    // field probes (diagnostic): weights, ring of E samples, device step counter
+    long long probe_n = 0, probe_cap = 0;
+    ProbeW *probe_w = nullptr;
+    double2 *probe_ring = nullptr;
+    unsigned long long *probe_count = nullptr;
+
     ~fetdpic_ctx()
     {
         cudaSetDevice(device);
@@ -123,6 +129,16 @@ struct fetdpic_ctx {
         if (!q) throw std::bad_alloc();
         allocs.push_back(q);
         return (T *)q;
+    }
+
+    // Frees one allocation made by alloc().
+    void release(void *q)
+    {
+        if (!q) return;
+        for (size_t k = 0; k < allocs.size(); ++k)
+            if (allocs[k] == q) { allocs.erase(allocs.begin() + k); break; }
+        if (p.dev_free) p.dev_free(q, p.alloc_user);
+        else cudaFree(q);
     }
 
     int fail(int code, const std::string &m)
@@ -754,6 +770,11 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     A.e = ctx->e;
     launch_ampere(ctx->stream, A);
     launches += (ctx->E > 0) + (ctx->nfree > 0);
+    if (ctx->probe_n > 0) {
+        launch_probe(ctx->stream, ctx->probe_n, ctx->probe_w, ctx->e, ctx->probe_ring, ctx->probe_cap,
+                     ctx->probe_count);
+        ++launches;
+    }
     if (timed) mark(ctx, 3);
     if (check) {
         launch_dgl(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->qunit, ctx->d, ctx->q1, ctx->g0, 0,
@@ -1032,6 +1053,83 @@ extern "C" int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6])
     long long np = 0;
     for (auto &s : ctx->staged) if (s.inst == inst) np += (long long)s.cell.size();
     out[5] = np;
+    return FETDPIC_OK;
+}
+
+static void drop_graphs(fetdpic_ctx *ctx);
+
+extern "C" int fetdpic_set_probes(fetdpic_ctx *ctx, long long n, const int *inst, const double *xy,
+                                  long long capacity)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    if (n < 0 || (n > 0 && (!inst || !xy || capacity <= 0)) || n > (1ll << 24) ||
+        (n > 0 && (double)n * (double)capacity > 1e10))
+        return ctx->fail(FETDPIC_EINVAL, "bad probe arguments (n <= 2^24, n * capacity <= 1e10 samples)");
+    std::vector<ProbeW> w((size_t)n);
+    for (long long p = 0; p < n; ++p) {
+        const int k = inst[p];
+        if (k < 0 || k >= (int)ctx->mesh.size()) return ctx->fail(FETDPIC_EINVAL, "probe instance out of range");
+        const HostMesh &M = ctx->mesh[k];
+        const double x = xy[2 * p], y = xy[2 * p + 1];
+        const int f = host_locate(M, x, y, -1);
+        if (f < 0) return ctx->fail(FETDPIC_EOUTSIDE, "probe " + std::to_string(p) + " lies in no triangle");
+        double l[3];
+        host_lambdas(M, f, x, y, l);
+        ProbeW &W = w[(size_t)p];
+        for (int m = 0; m < 3; ++m) {
+            const int a = (m + 1) % 3, b = (m + 2) % 3;
+            const double sg = M.tsign[3 * f + m];
+            W.w[2 * m] = sg * (l[a] * M.gx[3 * f + b] - l[b] * M.gx[3 * f + a]);
+            W.w[2 * m + 1] = sg * (l[a] * M.gy[3 * f + b] - l[b] * M.gy[3 * f + a]);
+            W.eg[m] = ctx->edge_off[k] + M.tedge[3 * f + m];
+        }
+        W.pad = 0;
+    }
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->release(ctx->probe_w); ctx->release(ctx->probe_ring); ctx->release(ctx->probe_count);
+    ctx->probe_w = nullptr; ctx->probe_ring = nullptr; ctx->probe_count = nullptr;
+    ctx->probe_n = 0; ctx->probe_cap = 0;
+    drop_graphs(ctx);                          // the step's launch sequence changes
+    if (n == 0) return FETDPIC_OK;
+    try {
+        ctx->probe_w = ctx->alloc<ProbeW>((size_t)n);
+        ctx->probe_ring = ctx->alloc<double2>((size_t)n * (size_t)capacity);
+        ctx->probe_count = ctx->alloc<unsigned long long>(1);
+    } catch (const std::bad_alloc &) {
+        return ctx->fail(FETDPIC_ENOMEM, "probe buffers");
+    }
+    CK(cudaMemcpyAsync(ctx->probe_w, w.data(), sizeof(ProbeW) * (size_t)n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->probe_count, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->probe_n = n;
+    ctx->probe_cap = capacity;
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_read_probes(fetdpic_ctx *ctx, double *exy, long long max_rows, long long *rows,
+                                   long long *total)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    if (max_rows < 0 || (max_rows > 0 && !exy)) return ctx->fail(FETDPIC_EINVAL, "bad probe read arguments");
+    if (ctx->probe_n == 0) return ctx->fail(FETDPIC_ESTATE, "no probes set");
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned long long cnt = 0;
+    CK(cudaMemcpy(&cnt, ctx->probe_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    const long long have = std::min<long long>((long long)cnt, ctx->probe_cap);
+    const long long take = std::min(have, max_rows);
+    const size_t row_bytes = sizeof(double2) * (size_t)ctx->probe_n;
+    for (long long k = 0; k < take; ++k) {
+        // oldest of the last `take` rows first
+        const unsigned long long step = cnt - (unsigned long long)take + (unsigned long long)k;
+        const long long r = (long long)(step % (unsigned long long)ctx->probe_cap);
+        CK(cudaMemcpyAsync(exy + (size_t)k * 2 * (size_t)ctx->probe_n, ctx->probe_ring + (size_t)r * ctx->probe_n,
+                           row_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (rows) *rows = take;
+    if (total) *total = (long long)cnt;
     return FETDPIC_OK;
 }
 

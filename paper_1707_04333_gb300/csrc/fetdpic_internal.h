@@ -187,6 +187,11 @@ void launch_charge(cudaStream_t st, bool fp32, long long P, const int *cell, con
                    unsigned long long *q, int N);
 void launch_dce(cudaStream_t st, int N, const int *nrp, const int *nedge, const int *ninst,
                 const unsigned long long *ifix, const unsigned long long *q0, const unsigned long long *q1, double *out);
+// Field probe: E(x_p) = sum_m w_m e[eg_m], w_m = s_m (l_a grad l_b - l_b grad l_a)
+// at the probe's barycentrics (a = m+1, b = m+2), precomputed on the host.
+struct ProbeW { double w[6]; int eg[3]; int pad; };
+void launch_probe(cudaStream_t st, long long n, const ProbeW *pw, const double *e, double2 *ring, long long cap,
+                  unsigned long long *count);
 void launch_dgl(cudaStream_t st, int N, const int *nrp, const int *nedge, const int *ninst, const double *qunit,
                 const double *d, const unsigned long long *q, double *g0, int init, double *out);
 long long energy_blocks(int E, int F);

@@ -194,4 +194,30 @@ void launch_energy(cudaStream_t st, int E, int F, const long long *hrp, const in
     k_energy_final<<<(ninst + 63) / 64, 64, 0, st>>>(nb, ninst, part, out);
 }
 
+
+// ------------------------------------------------------------- field probes
+// One block: every thread reads the step counter before thread 0 advances it,
+// so a captured graph writes consecutive ring rows on consecutive replays.
+__global__ void __launch_bounds__(256) k_probe(long long n, const ProbeW *__restrict__ pw, const double *__restrict__ e,
+                                               double2 *__restrict__ ring, long long cap,
+                                               unsigned long long *count)
+{
+    const unsigned long long row = *count % (unsigned long long)cap;
+    double2 *out = ring + (size_t)row * (size_t)n;
+    for (long long p = threadIdx.x; p < n; p += blockDim.x) {
+        const ProbeW w = pw[p];
+        const double e0 = e[w.eg[0]], e1 = e[w.eg[1]], e2 = e[w.eg[2]];
+        out[p] = make_double2(w.w[0] * e0 + w.w[2] * e1 + w.w[4] * e2, w.w[1] * e0 + w.w[3] * e1 + w.w[5] * e2);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *count += 1;
+}
+
+void launch_probe(cudaStream_t st, long long n, const ProbeW *pw, const double *e, double2 *ring, long long cap,
+                  unsigned long long *count)
+{
+    if (n <= 0 || cap <= 0) return;
+    k_probe<<<1, 256, 0, st>>>(n, pw, e, ring, cap, count);
+}
+
 }  // namespace fetdpic

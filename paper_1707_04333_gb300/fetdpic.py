@@ -77,6 +77,8 @@ def lib():
             "fetdpic_check": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_info": (i32, [vp, i32, vp]),
             "fetdpic_read_edges": (i32, [vp, i32, vp]),
+            "fetdpic_set_probes": (i32, [vp, i64, vp, vp, i64]),
+            "fetdpic_read_probes": (i32, [vp, vp, i64, vp, vp]),
             "fetdpic_read_spai": (i32, [vp, i32, vp, vp, vp, vp]),
             "fetdpic_stage_times": (i32, [vp, vp, vp]),
             "fetdpic_autotune": (i32, [vp, i32, i32, vp, vp]),
@@ -198,6 +200,23 @@ def fetdpic_read_edges(h, inst=0):
     ed = np.zeros((info["n_edges"], 2), np.int32)
     _check(h, lib().fetdpic_read_edges(h, inst, _ptr(ed)))
     return ed
+
+
+def fetdpic_set_probes(h, xy, inst=None, capacity=4096):
+    """Field probes at points xy (n x 2, metres) of instances inst (default 0), recording the last
+    `capacity` steps on the device."""
+    xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+    n = len(xy)
+    inst = np.zeros(n, np.int32) if inst is None else np.ascontiguousarray(inst, np.int32)
+    _check(h, lib().fetdpic_set_probes(h, n, _ptr(inst), _ptr(xy), capacity))
+
+
+def fetdpic_read_probes(h, n, max_rows):
+    """(exy [rows][n][2] oldest first, total steps recorded)."""
+    out = np.zeros((max_rows, n, 2))
+    rows, total = C.c_longlong(), C.c_longlong()
+    _check(h, lib().fetdpic_read_probes(h, _ptr(out), max_rows, C.byref(rows), C.byref(total)))
+    return out[:rows.value], total.value
 
 
 def fetdpic_read_spai(h, inst=0):
@@ -376,6 +395,15 @@ class Simulation:
 
     def read_fields(self, inst=0):
         return fetdpic_read(self.h, inst, species=None, fields=True)
+
+    def set_probes(self, xy, inst=None, capacity=4096):
+        fetdpic_set_probes(self.h, xy, inst, capacity)
+        self._probe_n, self._probe_cap = len(np.asarray(xy).reshape(-1, 2)), capacity
+        return self
+
+    def read_probes(self, max_rows=None):
+        """E at the probes for the recorded steps, oldest first: (rows x n x 2, total steps)."""
+        return fetdpic_read_probes(self.h, self._probe_n, max_rows or self._probe_cap)
 
     def close(self):
         if self.h:

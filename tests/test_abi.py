@@ -39,4 +39,6 @@ def test_invalid_arguments_rejected_without_gpu(libmod):
     assert L.fetdpic_create(None, None, 0, None) == libmod.EINVAL
     assert L.fetdpic_step(None, 1, 0) == libmod.EINVAL
     assert L.fetdpic_sync(None) == libmod.EINVAL
+    assert L.fetdpic_set_probes(None, 0, None, None, 0) == libmod.EINVAL
+    assert L.fetdpic_read_probes(None, None, 0, None, None) == libmod.EINVAL
     assert L.fetdpic_last_error(None) == b"null context"
