@@ -51,7 +51,17 @@ typedef struct {
     double *inv2A;      /* [nf] 1/(2A) */
     double *gx, *gy;    /* [nf][3] grad lambda_m */
     double *nx_, *ny_;  /* [nf][3] node coordinates, copied per triangle */
+    /* periodic walls (NULL rep = none): node n is identified with node rep[n]
+     * (rep[n] == n for every node that is not an image); an image sits at its
+     * representative's position plus (tx, ty).  tri_shift[3f+m] in {-1,0,1}:
+     * crossing local edge m of triangle f translates the position by
+     * tri_shift * (tx, ty). */
+    const int *rep;
+    int *tri_shift;
+    double tx, ty;
 } ora_mesh;
+
+static inline int node_rep(const ora_mesh *M, int n) { return M->rep ? M->rep[n] : n; }
 
 /* ---------------------------------------------------------------- topology */
 
@@ -87,7 +97,9 @@ int ora_mesh_build(ora_mesh *M, const int *tri_in)
     if (!h) return ORA_EINVAL;
     for (int f = 0; f < nf; ++f)
         for (int m = 0; m < 3; ++m) {
-            int u = M->tri[3 * f + (m + 1) % 3], v = M->tri[3 * f + (m + 2) % 3];
+            /* edges join representative nodes: the two copies of a periodic edge are one edge */
+            int u = node_rep(M, M->tri[3 * f + (m + 1) % 3]), v = node_rep(M, M->tri[3 * f + (m + 2) % 3]);
+            if (u == v) { free(h); return ORA_EMESH; }      /* an edge joining a node to its own image */
             half_edge e;
             e.a = u < v ? u : v; e.b = u < v ? v : u; e.t = f; e.m = m;
             h[3 * f + m] = e;
@@ -104,11 +116,19 @@ int ora_mesh_build(ora_mesh *M, const int *tri_in)
             int f = h[r].t, m = h[r].m;
             M->tri_edge[3 * f + m] = ne;
             /* local edge runs node m+1 -> m+2 */
-            M->tri_sign[3 * f + m] = (M->tri[3 * f + (m + 1) % 3] == h[r].a) ? 1 : -1;
+            M->tri_sign[3 * f + m] = (node_rep(M, M->tri[3 * f + (m + 1) % 3]) == h[r].a) ? 1 : -1;
             M->tri_nb[3 * f + m] = -1;
+            if (M->tri_shift) M->tri_shift[3 * f + m] = 0;
             if (k2 - k == 2) {
                 const half_edge *o = &h[r == k ? k + 1 : k];
                 M->tri_nb[3 * f + m] = o->t;
+                if (M->tri_shift) {
+                    /* the neighbour's copy of our node m+1 is its node o->m + 2 (opposite
+                     * orientation); an image node lies one period beyond its representative */
+                    int a1 = M->tri[3 * f + (m + 1) % 3];
+                    int b2 = M->tri[3 * o->t + (o->m + 2) % 3];
+                    M->tri_shift[3 * f + m] = (b2 != node_rep(M, b2)) - (a1 != node_rep(M, a1));
+                }
             }
         }
         ++ne;
@@ -582,6 +602,12 @@ int ora_particles(const ora_mesh *M, const ora_step_params *P,
                 int m2 = 0;
                 while (m2 < 3 && M->tri_edge[3 * nb + m2] != eg) ++m2;
                 if (m2 == 3) { status = ORA_EMESH; break; }
+                /* periodic wall: the rest of the segment continues from the other copy */
+                int sc = M->tri_shift ? M->tri_shift[3 * f + best] : 0;
+                if (sc != 0) {
+                    xs = xs + sc * M->tx; ys = ys + sc * M->ty;
+                    xf = xf + sc * M->tx; yf = yf + sc * M->ty;
+                }
                 double l2[3];
                 l2[m2] = 0.0;
                 l2[(m2 + 1) % 3] = lout[(best + 2) % 3];
@@ -609,7 +635,7 @@ void ora_charge(const ora_mesh *M, double Q, int n, const double *x, const doubl
         double l[3];
         int f = cell[p];
         lambdas(M, f, x[p], y[p], l);
-        for (int k = 0; k < 3; ++k) q_node[M->tri[3 * f + k]] += Q * l[k];
+        for (int k = 0; k < 3; ++k) q_node[node_rep(M, M->tri[3 * f + k])] += Q * l[k];
     }
 }
 

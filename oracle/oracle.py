@@ -59,7 +59,8 @@ class _MeshC(C.Structure):
                 ("xy", C.c_void_p), ("tri", C.c_void_p), ("edge", C.c_void_p),
                 ("tri_edge", C.c_void_p), ("tri_sign", C.c_void_p), ("tri_nb", C.c_void_p),
                 ("edge_bnd", C.c_void_p), ("d2A", C.c_void_p), ("inv2A", C.c_void_p),
-                ("gx", C.c_void_p), ("gy", C.c_void_p), ("nx_", C.c_void_p), ("ny_", C.c_void_p)]
+                ("gx", C.c_void_p), ("gy", C.c_void_p), ("nx_", C.c_void_p), ("ny_", C.c_void_p),
+                ("rep", C.c_void_p), ("tri_shift", C.c_void_p), ("tx", C.c_double), ("ty", C.c_double)]
 
 
 class _StepC(C.Structure):
@@ -75,10 +76,30 @@ def _p(a):
 class OracleMesh:
     """Topology (incidence C, S~), orientation and Whitney geometry of a triangle mesh."""
 
-    def __init__(self, nodes, triangles):
+    def __init__(self, nodes, triangles, periodic=None):
+        """periodic = (pairs, (tx, ty)): pairs[k] = (node a, node b) with node b the image of node a
+        one period (tx, ty) away; the two nodes become one, and so do the edges they bound."""
         self.xy = np.ascontiguousarray(nodes, np.float64)
         tri_in = np.ascontiguousarray(triangles, np.int32)
         nn, nf = len(self.xy), len(tri_in)
+        self.rep = None
+        self.tri_shift = None
+        self.period = (0.0, 0.0)
+        if periodic is not None:
+            pairs, (tx, ty) = periodic
+            pairs = np.asarray(pairs, np.int64).reshape(-1, 2)
+            rep = np.arange(nn, dtype=np.int32)
+            span = float(np.abs(self.xy).max()) + abs(tx) + abs(ty)
+            for a, b in pairs:
+                if a == b or rep[b] != b or rep[a] != a:
+                    raise ValueError("periodic pairs must join distinct nodes, each image once")
+                d = self.xy[b] - self.xy[a] - (tx, ty)
+                if np.abs(d).max() > 1e-9 * span:
+                    raise ValueError(f"node {b} is not node {a} translated by the period")
+                rep[b] = a
+            self.rep = rep
+            self.tri_shift = np.zeros((nf, 3), np.int32)
+            self.period = (float(tx), float(ty))
         self.tri = np.zeros((nf, 3), np.int32)
         self.edge = np.zeros((3 * nf, 2), np.int32)
         self.tri_edge = np.zeros((nf, 3), np.int32)
@@ -93,7 +114,10 @@ class OracleMesh:
         self.ny = np.zeros((nf, 3))
         s = _MeshC(nn, nf, 0, _p(self.xy), _p(self.tri), _p(self.edge), _p(self.tri_edge),
                    _p(self.tri_sign), _p(self.tri_nb), _p(self.edge_bnd), _p(self.d2A),
-                   _p(self.inv2A), _p(self.gx), _p(self.gy), _p(self.nx), _p(self.ny))
+                   _p(self.inv2A), _p(self.gx), _p(self.gy), _p(self.nx), _p(self.ny),
+                   None if self.rep is None else _p(self.rep),
+                   None if self.tri_shift is None else _p(self.tri_shift),
+                   self.period[0], self.period[1])
         ne = lib().ora_mesh_build(C.byref(s), _p(tri_in))
         if ne < 0:
             raise ValueError(f"oracle: invalid mesh (status {ne})")
@@ -109,6 +133,16 @@ class OracleMesh:
     @property
     def cs(self):
         return C.byref(self._s)
+
+    def edge_vectors(self) -> np.ndarray:
+        """r_j - r_i of every edge (i -> j), read off a triangle that holds it (with periodic walls
+        the two nodes of an edge may be stored one period apart)."""
+        v = np.zeros((self.ne, 2))
+        for m in range(3):
+            a, b = (m + 1) % 3, (m + 2) % 3
+            d = np.stack([self.nx[:, b] - self.nx[:, a], self.ny[:, b] - self.ny[:, a]], axis=1)
+            v[self.tri_edge[:, m]] = d * self.tri_sign[:, m, None]
+        return v
 
     def curl(self) -> sp.csr_matrix:
         """C (faces x edges), entries in {-1,0,1}."""
@@ -197,9 +231,10 @@ class OracleSim:
     """
 
     def __init__(self, nodes, triangles, dt, *, eps0, mu0, c, spai_level=2, exact_inverse=False,
-                 b0=0.0, e0=(0.0, 0.0), ext=(0.0, 0.0, 0.0), max_cross=64, fields=True):
-        """fields=False skips [*eps] and the SPAI (particle-only steps on large meshes)."""
-        self.mesh = m = OracleMesh(nodes, triangles)
+                 b0=0.0, e0=(0.0, 0.0), ext=(0.0, 0.0, 0.0), max_cross=64, fields=True, periodic=None):
+        """fields=False skips [*eps] and the SPAI (particle-only steps on large meshes);
+        periodic: as for OracleMesh."""
+        self.mesh = m = OracleMesh(nodes, triangles, periodic)
         self.dt, self.eps0, self.mu0, self.c = dt, eps0, mu0, c
         self.ext = tuple(float(v) for v in ext)
         self.max_cross = max_cross
@@ -221,7 +256,7 @@ class OracleSim:
         self._v = np.ascontiguousarray(Minv.data, np.float64)
         # uniform initial fields: b_f = B0 A_f (flux), e_k = E0 . (r_j - r_i) on free edges
         self.b = b0 * (0.5 * m.d2A)
-        t = m.xy[m.edge[:, 1]] - m.xy[m.edge[:, 0]]
+        t = m.edge_vectors()
         self.e = (e0[0] * t[:, 0] + e0[1] * t[:, 1]) * (m.edge_bnd == 0)
         self.d = self.star_eps @ self.e
         self.i = np.zeros(m.ne)

@@ -32,6 +32,8 @@ class Mesh:
     triangles: np.ndarray  # [F,3] int32, counter-clockwise
     lx: float
     ly: float
+    # periodic walls: (pairs [k,2] int32, (tx, ty)); node pairs[k,1] is node pairs[k,0] moved by (tx, ty)
+    periodic: object = None
 
 
 @dataclasses.dataclass
@@ -60,12 +62,14 @@ class Workload:
 
 
 def jittered_delaunay(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0,
-                      jitter: float = 0.3, seed: int = 1) -> Mesh:
+                      jitter: float = 0.3, seed: int = 1, periodic_y: bool = False) -> Mesh:
     """Delaunay mesh of an (nx+1) x (ny+1) grid of jittered points on [0,lx]x[0,ly].
 
     Interior points move by up to +-jitter*h in each direction; boundary points
     slide only along their side and corners stay fixed, so the hull is the
-    rectangle.  About 2*nx*ny triangles.
+    rectangle.  About 2*nx*ny triangles.  periodic_y: the top row repeats the
+    bottom row's x positions and Mesh.periodic pairs each bottom node with the
+    top node above it, period (0, ly).
     """
     import scipy.spatial
 
@@ -80,6 +84,8 @@ def jittered_delaunay(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0,
     on_y_side = (jj == 0) | (jj == ny)
     jx[on_x_side] = 0.0
     jy[on_y_side] = 0.0
+    if periodic_y:
+        jx[:, ny] = jx[:, 0]
     x = x + jx
     y = y + jy
     pts = np.stack([x.ravel(), y.ravel()], 1)
@@ -90,7 +96,11 @@ def jittered_delaunay(nx: int, ny: int, lx: float = 1.0, ly: float = 1.0,
     tri[cw] = tri[cw][:, [0, 2, 1]]
     keep = o != 0
     tri = np.ascontiguousarray(tri[keep])
-    return Mesh(np.ascontiguousarray(pts), tri, lx, ly)
+    periodic = None
+    if periodic_y:
+        col = np.arange(nx + 1) * (ny + 1)                  # node id of grid point (i, j) = i (ny+1) + j
+        periodic = (np.stack([col, col + ny], 1).astype(np.int32), (0.0, float(ly)))
+    return Mesh(np.ascontiguousarray(pts), tri, lx, ly, periodic)
 
 
 def sample_in_triangles(mesh: Mesh, tri_ids: np.ndarray, rng) -> np.ndarray:
@@ -148,10 +158,12 @@ def cyclotron(gamma: float = 2.0, n: int = 64, nx: int = 32, seed: int = 1,
 
 def pair_plasma(n_tri_side: int = 317, ppc: int = 20, kT: float = 0.1,
                 wc_over_wp: float = 0.5, courant: float = 0.2, seed: int = 2,
-                pusher: str = "vay") -> Workload:
+                pusher: str = "vay", ny: int | None = None, periodic_y: bool = False) -> Workload:
     """Magnetized electron-positron pair plasma (the paper's Bernstein-mode case shape).
 
-    Mesh: jittered Delaunay of (n+1)^2 points, about 2 n^2 triangles, PEC walls.
+    Mesh: jittered Delaunay of (n+1)^2 points, about 2 n^2 triangles, PEC walls
+    (ny rows instead of n gives an n x ny strip; periodic_y joins its top and
+    bottom walls, the paper's Bernstein geometry with PEC in place of PML).
     Side length set so the mean edge length is about one Debye length
     lambda_D ~ v_th/omega_p.  ppc particles per species per triangle, each
     electron collocated with a positron of opposite momentum (2-D
@@ -166,14 +178,16 @@ def pair_plasma(n_tri_side: int = 317, ppc: int = 20, kT: float = 0.1,
     lam_d = vth / wp
     h = lam_d
     side = h * n_tri_side
-    mesh = jittered_delaunay(n_tri_side, n_tri_side, side, side, 0.3, seed)
+    nyr = n_tri_side if ny is None else ny
+    side_y = h * nyr
+    mesh = jittered_delaunay(n_tri_side, nyr, side, side_y, 0.3, seed, periodic_y=periodic_y)
     rng = np.random.default_rng(seed + 1000)
     nf = len(mesh.triangles)
     tri_ids = np.repeat(np.arange(nf, dtype=np.int32), ppc)
     x = sample_in_triangles(mesh, tri_ids, rng)
     u = maxwell_juttner_2d(len(x), 1.0 / kT, rng)
     dens = wp * wp * EPS0 * M_E / (Q_E * Q_E)      # per m^3; per unit depth -> per m^2 * 1 m
-    area = side * side
+    area = side * side_y
     weight = dens * area / len(x)
     e_sp = Species(-Q_E * weight, M_E * weight, x, u, tri_ids.copy())
     p_sp = Species(+Q_E * weight, M_E * weight, x.copy(), -u, tri_ids.copy())
