@@ -128,6 +128,19 @@ typedef struct {
     double b0;               /* initial uniform B_z: b_f = b0 * area_f (face DoF, Eq. (B)) */
     double e0x, e0y;         /* initial uniform E on free edges: e_k = E0 . (r_j - r_i) (Eq. (E)) */
     double ext_ex, ext_ey, ext_bz; /* external uniform fields added at each particle */
+    /* Optional periodic walls (the paper's Bernstein strip is periodic top and
+     * bottom, Sec. III.C): n_periodic node pairs (a, b) in periodic_nodes
+     * [n_periodic][2], node b lying at node a + (period_x, period_y) within
+     * 1e-9 of the mesh extent.  Each b becomes the same node as its a, so the
+     * two copies of a wall edge are one edge (one e unknown, two triangles);
+     * a particle crossing it continues from the other copy, translated by the
+     * period, with the same momentum.  Requires edges == NULL and
+     * edge_tags == NULL (the remaining boundary edges are PEC).  Each node is
+     * an image at most once and no triangle may join a node to its image
+     * (EMESH).  n_periodic = 0: no periodic walls. */
+    int n_periodic;
+    const int *periodic_nodes;
+    double period_x, period_y;
 } fetdpic_instance;
 
 /* Build the mesh topology, incidence matrices C and S~ (Sec. II.A), Whitney

@@ -71,6 +71,8 @@ struct fetdpic_ctx {
     void *f[4] = {nullptr, nullptr, nullptr, nullptr}, *f_tmp[4] = {nullptr, nullptr, nullptr, nullptr};
     short *blk_sp = nullptr;
     short *chunk_sp = nullptr;               // species of each 32-particle chunk
+    signed char *tshift = nullptr;           // periodic shift codes (FP64 walk), NULL without periodic walls
+    double2 *period = nullptr;               // per instance
     int *hist = nullptr, *hoff = nullptr, *scan_tmp = nullptr; long long hist_n = 0;
     long long *pad_adj = nullptr;
     int *rec_cnt = nullptr, *rec = nullptr;
@@ -213,7 +215,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         if (!(I.dt > 0)) return ctx->fail(FETDPIC_EINVAL, "dt must be > 0"), FETDPIC_EINVAL;
         std::string msg;
         int rc = build_mesh(ctx->mesh[k], I.n_nodes, I.nodes_xy, I.n_tri, I.triangles,
-                            I.edges ? I.n_edges : 0, I.edges, I.edge_tags, msg);
+                            I.edges ? I.n_edges : 0, I.edges, I.edge_tags,
+                            I.n_periodic, I.periodic_nodes, I.period_x, I.period_y, msg);
         if (rc == FETDPIC_OK) rc = build_hodge(ctx->mesh[k], P.eps0, msg);
         if (rc == FETDPIC_OK) rc = build_spai(ctx->mesh[k], P.spai_level, msg);
         if (rc != FETDPIC_OK) {
@@ -263,7 +266,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
                 const int eg = eo + M.tedge[3 * f + m];
                 T.ew[m] = (eg << 1) | (M.tsign[3 * f + m] < 0 ? 1 : 0);
                 T.nb[m] = M.tnb[3 * f + m] < 0 ? -1 : (((co + M.tnb[3 * f + m]) << 2) | M.tnbm[3 * f + m]);
-                T.node[m] = no + M.tri[3 * f + m];
+                T.node[m] = no + M.rep[M.tri[3 * f + m]];
             }
             T.inst = k;
             b0[co + f] = I.b0 * (0.5 * M.d2A[f]);          // b_f = B0 A_f
@@ -279,9 +282,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             }
         }
         for (int e = 0; e < M.ne; ++e) {
-            const int a = M.edge[2 * e], bnode = M.edge[2 * e + 1];
-            if (!M.pec[e])
-                e0[eo + e] = I.e0x * (M.xy[2 * bnode] - M.xy[2 * a]) + I.e0y * (M.xy[2 * bnode + 1] - M.xy[2 * a + 1]);
+            if (!M.pec[e]) e0[eo + e] = I.e0x * M.evec[2 * e] + I.e0y * M.evec[2 * e + 1];
             efac[eo + e] = make_int2(co + M.efac[2 * e], M.efac[2 * e + 1] < 0 ? -1 : co + M.efac[2 * e + 1]);
             const double h0 = 1.0 / (P.mu0 * (0.5 * M.d2A[M.efac[2 * e]]));
             const double h1 = M.efac[2 * e + 1] < 0 ? 0.0 : 1.0 / (P.mu0 * (0.5 * M.d2A[M.efac[2 * e + 1]]));
@@ -303,6 +304,18 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             mrp.push_back((long long)mci.size());
         }
     }
+    // periodic walls: shift codes of every (triangle, local edge) and the period of each instance
+    bool any_periodic = false;
+    for (int k = 0; k < n_inst; ++k) any_periodic = any_periodic || ctx->mesh[k].periodic;
+    std::vector<signed char> tsh(any_periodic ? 3 * (size_t)ctx->F : 0, 0);
+    std::vector<double2> per(any_periodic ? n_inst : 0);
+    if (any_periodic)
+        for (int k = 0; k < n_inst; ++k) {
+            const HostMesh &M = ctx->mesh[k];
+            per[k] = make_double2(M.tx, M.ty);
+            if (M.periodic)
+                std::copy(M.tshift.begin(), M.tshift.end(), tsh.begin() + 3 * (size_t)ctx->cell_off[k]);
+        }
     ctx->nfree = (long long)mrow.size();
     // sliced ELL (32 rows per slice, column-major inside a slice)
     std::vector<long long> soff(1, 0);
@@ -388,6 +401,10 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         ctx->inst_unit = ctx->alloc<double>(n_inst);
         ctx->inst_dt = ctx->alloc<double>(n_inst);
         ctx->edge_off_dev = ctx->alloc<int>(n_inst + 1);
+        if (any_periodic) {
+            ctx->tshift = ctx->alloc<signed char>(3 * (size_t)ctx->F);
+            ctx->period = ctx->alloc<double2>(n_inst);
+        }
         ctx->m_soff = ctx->alloc<long long>(soff.size());
         ctx->m_row = ctx->alloc<int>(mrow.size());
         ctx->m_ci = ctx->alloc<int>(sci.size());
@@ -438,6 +455,10 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     rc = rc ? rc : upload(ctx, ctx->einst, einst.data(), einst.size());
     rc = rc ? rc : upload(ctx, ctx->inst_dt, idt.data(), idt.size());
     rc = rc ? rc : upload(ctx, ctx->edge_off_dev, ctx->edge_off.data(), ctx->edge_off.size());
+    if (any_periodic) {
+        rc = rc ? rc : upload(ctx, ctx->tshift, tsh.data(), tsh.size());
+        rc = rc ? rc : upload(ctx, ctx->period, per.data(), per.size());
+    }
     rc = rc ? rc : upload(ctx, ctx->m_soff, soff.data(), soff.size());
     rc = rc ? rc : upload(ctx, ctx->m_row, mrow.data(), mrow.size());
     rc = rc ? rc : upload(ctx, ctx->m_ci, sci.data(), sci.size());
@@ -671,6 +692,7 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
     a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec;
     a.edge_off = ctx->edge_off_dev;
     a.nblocks = ctx->nblocks; a.block = ctx->block;
+    a.tshift = ctx->tshift; a.period = ctx->period;
     return a;
 }
 

@@ -28,6 +28,13 @@ struct HostMesh {
     std::vector<int> efsign;                // [ne][2] circulation sign of the edge in each triangle
     std::vector<double> d2A, inv2A;         // [nf]
     std::vector<double> gx, gy, X, Y;       // [nf][3] grad lambda_m, node coordinates
+    // periodic walls: node n is the same node as rep[n]; crossing local edge m of
+    // triangle f moves a position by tshift[3f+m] * (tx, ty)
+    bool periodic = false;
+    std::vector<int> rep;                   // [nn]
+    std::vector<signed char> tshift;        // [nf][3] in {-1, 0, 1}
+    double tx = 0.0, ty = 0.0;
+    std::vector<double> evec;               // [ne][2] r_j - r_i read off a triangle holding the edge
     // [*eps] restricted to free edges, CSR over free-edge indices
     std::vector<int> free_edges;            // ascending edge ids
     std::vector<long long> a_rp; std::vector<int> a_ci; std::vector<double> a_v;
@@ -39,7 +46,8 @@ struct HostMesh {
 
 // Returns 0 or a negative fetdpic_status; msg gets a reason on error.
 int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri,
-               int ne_in, const int *edges_in, const int *tags_in, std::string &msg);
+               int ne_in, const int *edges_in, const int *tags_in,
+               int n_per, const int *per_nodes, double tx, double ty, std::string &msg);
 int build_hodge(HostMesh &M, double eps0, std::string &msg);
 int build_spai(HostMesh &M, int level, std::string &msg);
 
@@ -123,6 +131,8 @@ struct StepArgs64 {
     int rec_cap; int *rec_cnt; int *wrec;   // walk record (rec_cap = 0: off)
     const int *edge_off;                    // per instance, for instance-local record ids
     long long nblocks; int block;
+    const signed char *tshift;              // [F][3] periodic shift codes; NULL = no periodic walls
+    const double2 *period;                  // per instance (tx, ty)
 };
 
 struct StepArgs32 {

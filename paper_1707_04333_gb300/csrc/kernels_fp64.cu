@@ -268,6 +268,15 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
                     l2[(m2 + 1) % 3] = lout[(best + 2) % 3];
                     l2[(m2 + 2) % 3] = lout[(best + 1) % 3];
                     lin[0] = l2[0]; lin[1] = l2[1]; lin[2] = l2[2];
+                    if (a.tshift) {
+                        // periodic wall: the rest of the segment continues from the other copy
+                        const int sc = a.tshift[3 * f + best];
+                        if (sc != 0) {
+                            const double2 T = a.period[tc.inst];
+                            xs = xs + sc * T.x; ys = ys + sc * T.y;
+                            xf = xf + sc * T.x; yf = yf + sc * T.y;
+                        }
+                    }
                     f = g2;
                     min = m2;
                     tin = tb;
@@ -360,6 +369,14 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
             l2[(m2 + 1) % 3] = lout[(best + 2) % 3];
             l2[(m2 + 2) % 3] = lout[(best + 1) % 3];
             lin[0] = l2[0]; lin[1] = l2[1]; lin[2] = l2[2];
+            if (a.tshift) {
+                const int sc = a.tshift[3 * f + best];
+                if (sc != 0) {
+                    const double2 T = a.period[tc.inst];
+                    xs = xs + sc * T.x; ys = ys + sc * T.y;
+                    xf = xf + sc * T.x; yf = yf + sc * T.y;
+                }
+            }
             f = g2;
             min = m2;
             tin = tb;

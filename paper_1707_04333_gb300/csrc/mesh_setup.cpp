@@ -23,11 +23,35 @@ static inline long long pair_key(int a, int b)
 }
 
 int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
-               int ne_in, const int *edges_in, const int *tags_in, std::string &msg)
+               int ne_in, const int *edges_in, const int *tags_in,
+               int n_per, const int *per_nodes, double tx, double ty, std::string &msg)
 {
     if (nn <= 0 || nf <= 0 || !xy || !tri_in) { msg = "empty mesh"; return FETDPIC_EINVAL; }
     M.nn = nn; M.nf = nf;
     M.xy.assign(xy, xy + 2 * (size_t)nn);
+    // periodic walls: each image node becomes its representative (Sec. III.C strip)
+    M.rep.resize(nn);
+    for (int n = 0; n < nn; ++n) M.rep[n] = n;
+    M.periodic = n_per > 0;
+    M.tx = tx; M.ty = ty;
+    if (n_per < 0 || (n_per > 0 && !per_nodes)) { msg = "bad periodic node list"; return FETDPIC_EINVAL; }
+    if (M.periodic) {
+        if (edges_in || tags_in) { msg = "periodic walls need derived edges and tags"; return FETDPIC_EINVAL; }
+        if (!(std::isfinite(tx) && std::isfinite(ty)) || (tx == 0.0 && ty == 0.0)) {
+            msg = "periodic walls need a nonzero period"; return FETDPIC_EINVAL;
+        }
+        double ext = std::fabs(tx) + std::fabs(ty);
+        for (int n = 0; n < nn; ++n) ext = std::max(ext, std::max(std::fabs(xy[2 * n]), std::fabs(xy[2 * n + 1])));
+        for (int k = 0; k < n_per; ++k) {
+            const int a = per_nodes[2 * k], b = per_nodes[2 * k + 1];
+            if (a < 0 || b < 0 || a >= nn || b >= nn || a == b) { msg = "periodic pair " + std::to_string(k) + " out of range"; return FETDPIC_EINVAL; }
+            if (M.rep[b] != b || M.rep[a] != a) { msg = "node in more than one periodic pair role"; return FETDPIC_EINVAL; }
+            if (std::fabs(xy[2 * b] - xy[2 * a] - tx) > 1e-9 * ext || std::fabs(xy[2 * b + 1] - xy[2 * a + 1] - ty) > 1e-9 * ext) {
+                msg = "periodic pair " + std::to_string(k) + ": node b is not node a moved by the period"; return FETDPIC_EMESH;
+            }
+            M.rep[b] = a;
+        }
+    }
     M.tri.resize(3 * (size_t)nf);
     for (int f = 0; f < nf; ++f) {
         int v[3] = {tri_in[3 * f], tri_in[3 * f + 1], tri_in[3 * f + 2]};
@@ -57,8 +81,11 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
     } else {
         keys.reserve(3 * (size_t)nf);
         for (int f = 0; f < nf; ++f)
-            for (int m = 0; m < 3; ++m)
-                keys.push_back(pair_key(M.tri[3 * f + (m + 1) % 3], M.tri[3 * f + (m + 2) % 3]));
+            for (int m = 0; m < 3; ++m) {
+                const int a = M.rep[M.tri[3 * f + (m + 1) % 3]], b = M.rep[M.tri[3 * f + (m + 2) % 3]];
+                if (a == b) { msg = "triangle " + std::to_string(f) + " joins a node to its periodic image"; return FETDPIC_EMESH; }
+                keys.push_back(pair_key(a, b));
+            }
         std::sort(keys.begin(), keys.end());
         keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
         M.ne = (int)keys.size();
@@ -74,7 +101,7 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
     M.efsign.assign(2 * (size_t)ne, 0);
     for (int f = 0; f < nf; ++f)
         for (int m = 0; m < 3; ++m) {
-            int a = M.tri[3 * f + (m + 1) % 3], b = M.tri[3 * f + (m + 2) % 3];
+            int a = M.rep[M.tri[3 * f + (m + 1) % 3]], b = M.rep[M.tri[3 * f + (m + 2) % 3]];
             long long k = pair_key(a, b);
             int e;
             if (edges_in) {
@@ -96,6 +123,7 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
             msg = "inconsistent orientation across edge " + std::to_string(e); return FETDPIC_EMESH;
         }
     }
+    M.tshift.assign(3 * (size_t)nf, 0);
     for (int f = 0; f < nf; ++f)
         for (int m = 0; m < 3; ++m) {
             int e = M.tedge[3 * f + m];
@@ -103,6 +131,13 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
             M.tnb[3 * f + m] = g;
             if (g >= 0)
                 for (int m2 = 0; m2 < 3; ++m2) if (M.tedge[3 * g + m2] == e) M.tnbm[3 * f + m] = m2;
+            if (g >= 0 && M.periodic) {
+                // the neighbour's copy of our node m+1 is its node m2+2; an image node lies one
+                // period beyond its representative
+                const int a1 = M.tri[3 * f + (m + 1) % 3];
+                const int b2 = M.tri[3 * g + (M.tnbm[3 * f + m] + 2) % 3];
+                M.tshift[3 * f + m] = (signed char)((M.rep[b2] != b2) - (M.rep[a1] != a1));
+            }
         }
     M.pec.assign(ne, 0);
     for (int e = 0; e < ne; ++e) {
@@ -126,6 +161,18 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
             M.Y[3 * f + m] = Y[m];
         }
     }
+    // edge vectors from the geometry of a triangle holding the edge (the two
+    // stored nodes of a periodic edge may be a period apart)
+    M.evec.assign(2 * (size_t)ne, 0.0);
+    for (int f = 0; f < nf; ++f)
+        for (int m = 0; m < 3; ++m) {
+            const int e = M.tedge[3 * f + m];
+            if (M.efac[2 * e] != f) continue;
+            const int a = (m + 1) % 3, b = (m + 2) % 3;
+            const double sg = M.tsign[3 * f + m];
+            M.evec[2 * e] = sg * (M.X[3 * f + b] - M.X[3 * f + a]);
+            M.evec[2 * e + 1] = sg * (M.Y[3 * f + b] - M.Y[3 * f + a]);
+        }
     M.free_edges.clear();
     for (int e = 0; e < ne; ++e) if (!M.pec[e]) M.free_edges.push_back(e);
     return FETDPIC_OK;

@@ -39,7 +39,8 @@ class Instance(C.Structure):
                 ("triangles", C.c_void_p), ("n_edges", C.c_int), ("edges", C.c_void_p),
                 ("edge_tags", C.c_void_p), ("dt", C.c_double), ("b0", C.c_double),
                 ("e0x", C.c_double), ("e0y", C.c_double), ("ext_ex", C.c_double),
-                ("ext_ey", C.c_double), ("ext_bz", C.c_double)]
+                ("ext_ey", C.c_double), ("ext_bz", C.c_double), ("n_periodic", C.c_int),
+                ("periodic_nodes", C.c_void_p), ("period_x", C.c_double), ("period_y", C.c_double)]
 
 
 class FetdpicError(RuntimeError):
@@ -332,6 +333,12 @@ class Simulation:
             I.dt, I.b0 = w.dt, w.b0
             I.e0x, I.e0y = w.e0
             I.ext_ex, I.ext_ey, I.ext_bz = w.ext
+            per = getattr(w.mesh, "periodic", None)
+            if per is not None:
+                pairs = np.ascontiguousarray(per[0], np.int32).reshape(-1, 2)
+                self._keep.append(pairs)
+                I.n_periodic, I.periodic_nodes = len(pairs), _ptr(pairs)
+                I.period_x, I.period_y = float(per[1][0]), float(per[1][1])
             insts.append(I)
         self.params = p
         self.h = fetdpic_create(p, insts)
