@@ -109,9 +109,6 @@ def test_probe_outside_mesh_rejected(fx):
     sim.close()
 
 
-BERNSTEIN_STEPS = 16384
-
-
 def _kinetic(species_list):
     """sum over particles of m c^2 (gamma - 1), gamma = sqrt(1 + |u|^2 / c^2) (superparticle mass m)."""
     c = inputs.C_LIGHT
@@ -119,7 +116,7 @@ def _kinetic(species_list):
                for m, u in species_list)
 
 
-def bernstein_run(fetdpic, w, precision, n_probes=128, steps=BERNSTEIN_STEPS):
+def bernstein_run(fetdpic, w, precision, n_probes, steps):
     """(k, omega, P) of E_x on a line across the middle, and (kinetic, field) energy changes over the
     run relative to the initial kinetic energy (field energy of the uniform B0 subtracted)."""
     L = w.mesh.lx
@@ -139,26 +136,39 @@ def bernstein_run(fetdpic, w, precision, n_probes=128, steps=BERNSTEIN_STEPS):
     return bernstein.spectrum(rows[:, :, 0], L / n_probes, w.dt), ((k1 - k0) / k0, (w1 - w0) / k0)
 
 
-def test_bernstein_band_frequencies_fp32_vs_fp64(fx):
-    """Pair plasma (8,192 triangles, 327,680 particles, kT = 0.1 mc^2, omega_c/omega_p = 0.5):
-    E_x on a line of 128 probes for 16,384 steps in each precision, the (k, omega) power of each,
-    and the power-weighted frequency of the first four cyclotron-harmonic bands.  The FP32 path's
-    band frequencies agree with the FP64 path's within one frequency bin of the record
-    (2 pi / (N dt) = 0.029 omega_c); the two runs start from the same state and diverge only through
-    rounding.  Energy: the kinetic and field energy changes over the run (units of the initial
-    kinetic energy K0; the same self-heating in both) agree within 1e-3 K0 between the precisions
-    (measured on GB300: total +0.51 % K0 in FP64, +0.49 % in FP32)."""
+BERNSTEIN_CASES = {
+    # PEC square, 8,192 triangles, 327,680 particles, kT = 0.1 mc^2, omega_c/omega_p = 0.5
+    "square": (lambda: inputs.pair_plasma(64, 20, kT=0.1, wc_over_wp=0.5, seed=2, pusher="vay"),
+               128, 16384, (1, 2, 3, 4)),
+    # the paper's geometry (Sec. III.C): a 1024 x 4 strip periodic top and bottom (PEC in place of
+    # PML at the ends), 8,192 triangles, 327,680 particles, kT = 0.05 mc^2, omega_p = 3 omega_c
+    "periodic-strip": (lambda: inputs.pair_plasma(1024, 20, kT=0.05, wc_over_wp=1 / 3, seed=6, pusher="vay",
+                                                  ny=4, periodic_y=True),
+                       256, 32768, (1, 2, 3, 4, 5)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(BERNSTEIN_CASES))
+def test_bernstein_band_frequencies_fp32_vs_fp64(fx, case):
+    """Pair plasma, E_x on a line of probes every step in each precision, the (k, omega) power of
+    each, and the power-weighted frequency of each cyclotron-harmonic band [(n - 1/2) omega_c,
+    (n + 1/2) omega_c).  The FP32 path's band frequencies agree with the FP64 path's within one
+    frequency bin of the record (2 pi / (N dt)); the two runs start from the same state and
+    diverge only through rounding.  Energy: the kinetic and field energy changes over the run
+    (units of the initial kinetic energy K0; the same self-heating in both) agree within 1e-3 K0
+    between the precisions."""
     fetdpic, _ = fx
-    w = inputs.pair_plasma(64, 20, kT=0.1, wc_over_wp=0.5, seed=2, pusher="vay")
+    make, n_probes, steps, bands = BERNSTEIN_CASES[case]
+    w = make()
     wc = inputs.Q_E * w.b0 / inputs.M_E
-    (k, om, P64), en64 = bernstein_run(fetdpic, w, "fp64")
-    (_, _, P32), en32 = bernstein_run(fetdpic, w, "fp32")
-    c64 = bernstein.band_centroids(k, om, P64, wc, harmonics=(1, 2, 3, 4))
-    c32 = bernstein.band_centroids(k, om, P32, wc, harmonics=(1, 2, 3, 4))
-    res = 2 * math.pi / (BERNSTEIN_STEPS * w.dt)
+    (k, om, P64), en64 = bernstein_run(fetdpic, w, "fp64", n_probes, steps)
+    (_, _, P32), en32 = bernstein_run(fetdpic, w, "fp32", n_probes, steps)
+    c64 = bernstein.band_centroids(k, om, P64, wc, harmonics=bands)
+    c32 = bernstein.band_centroids(k, om, P32, wc, harmonics=bands)
+    res = 2 * math.pi / (steps * w.dt)
     err = np.abs(c32 - c64) / wc
-    print("band centroids / wc fp64", c64 / wc, "fp32", c32 / wc, "error / wc", err, "bin / wc", res / wc)
-    print("energy change / K0 (kinetic, field, total) fp64", en64, sum(en64), "fp32", en32, sum(en32))
+    print(case, "band centroids / wc fp64", c64 / wc, "fp32", c32 / wc, "error / wc", err, "bin / wc", res / wc)
+    print(case, "energy change / K0 (kinetic, field, total) fp64", en64, sum(en64), "fp32", en32, sum(en32))
     assert np.isfinite(c64).all() and np.isfinite(c32).all()
     assert (err < res / wc).all(), err
     assert abs(sum(en32) - sum(en64)) < 1e-3, (en32, en64)
