@@ -251,17 +251,19 @@ def main():
     w = max(ws, key=lambda x: x.n_particles)     # the instance the CPU baseline samples
     stream = torch.cuda.Stream()          # explicit stream: the context's kernels and the timing events
 
-    graphs = args.workload == "cyclotron"        # launch-bound: replay captured graphs, no stage events
-
-    def timed_run(precision, steps, warmup, stages=not graphs):
-        sim = fetdpic.Simulation(ws, precision=precision, spai_level=2, sort_interval=args.sort_interval,
-                                 time_stages=stages, stream=stream, kernel_variant=args.variant,
-                                 use_graphs=graphs)
+    def timed_run(precision, steps, warmup, stages, graphs, tuned=None):
+        """Timed steps on the context stream.  graphs: replay captured one-step graphs (the
+        headline: no launch gaps, no stage events); stages: plain launches with CUDA events between
+        stages (the stage breakdown and the particle kernel's own time)."""
+        sim = fetdpic.Simulation(ws, precision=precision, spai_level=2,
+                                 sort_interval=tuned[1] if tuned else args.sort_interval,
+                                 time_stages=stages, stream=stream,
+                                 kernel_variant=tuned[0] if tuned else args.variant, use_graphs=graphs)
         sim.load()
-        if args.variant == 0 and not args.no_tune:
+        if tuned is None and args.variant == 0 and not args.no_tune:
             tuned = sim.autotune(args.pusher, trial_steps=32,
                                  cache=os.path.join(ROOT, "paper_1707_04333_gb300", "_build", "tuning.json"))
-        else:
+        elif tuned is None:
             tuned = (args.variant, args.sort_interval)
         sim.tuned = tuned
         sim.step(warmup, args.pusher).sync()
@@ -290,14 +292,18 @@ def main():
         pass
     clocks = ClockSampler(dev_id)
 
-    # ---- headline: FP32 path
+    # ---- headline: FP32 path, steps replayed from captured graphs
     clocks.start()
-    sim, ms, st, launches, pbytes, npart = timed_run("fp32", args.steps, args.warmup)
+    sim, ms, _, launches, pbytes, npart = timed_run("fp32", args.steps, args.warmup, stages=False, graphs=True)
     clk = clocks.stop()
     if world > 1:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    # ---- the same workload and tuning with CUDA events between stages (breakdown, roofline)
+    ks = min(args.steps, 500)
+    sim_st, ms_st, st, _, _, _ = timed_run("fp32", ks, args.warmup, stages=True, graphs=False, tuned=sim.tuned)
+    sim_st.close()
     K = args.steps
     value = npart * K * world / (ms / 1e3)
     part_ms = st[1] / max(st[3], 1) if st[3] > 0 else 0.0
@@ -309,7 +315,9 @@ def main():
                 "kernel": "k_particles32 (gather+push+walk+deposit)", "peak_kind": peak_kind,
                 "bytes_per_launch": pbytes, "traffic_source": traffic_note}
     stages = {"faraday_ms": st[0] / max(st[3], 1), "particles_ms": part_ms,
-              "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1)}
+              "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1),
+              "run": f"{ks} plain-launch steps with CUDA events between stages, "
+                     f"{ms_st / ks:.4f} ms per step (the headline replays captured graphs)"}
 
     # ---- end to end through the C ABI with page-locked host buffers
     e2e = None
@@ -353,7 +361,8 @@ def main():
     fp64 = None
     if not args.no_fp64:
         k64 = args.fp64_steps or min(args.steps, 100)
-        sim64, ms64, st64, l64, pb64, np64 = timed_run("fp64", k64, min(args.warmup, 3))
+        sim64, ms64, st64, l64, pb64, np64 = timed_run("fp64", k64, min(args.warmup, 3), stages=True,
+                                                       graphs=False, tuned=(3, sim.tuned[1]))
         if world > 1:
             t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
