@@ -392,7 +392,7 @@ def main():
                        "tuning": {"kernel_variant": sim_tuned[0], "sort_interval": sim_tuned[1]},
                        "triangles": sum(len(x.mesh.triangles) for x in ws), "particles_per_gpu": npart,
                        "instances": len(ws),
-                       "l2": "inputs larger than L2 (particle state 2 x 161 MB per step)",
+                       "l2": f"inputs larger than L2 (particle state 2 x {pbytes / 2e6:.0f} MB per step, L2 129 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline,
             "stages_ms_per_step": stages,

@@ -786,7 +786,9 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     AmpereArgs A{};
     A.E = ctx->E; A.efac = ctx->efac; A.ecoef = ctx->ecoef; A.einst = ctx->einst;
     A.inst_unit = ctx->inst_unit; A.inst_dt = ctx->inst_dt; A.b = ctx->b; A.ifix = ctx->ifix;
-    A.r = ctx->r; A.d = ctx->d; A.j = ctx->j; A.r32 = ctx->r32;
+    // FP32 mode reads r32 only; without checks nothing reads the dual flux d
+    A.r = f32 ? nullptr : ctx->r; A.d = ctx->p.check_interval > 0 ? ctx->d : nullptr;
+    A.j = ctx->j; A.r32 = ctx->r32;
     A.nfree = ctx->nfree; A.m_soff = ctx->m_soff; A.m_row = ctx->m_row; A.m_ci = ctx->m_ci; A.m_v = ctx->m_v;
     A.m_v32 = ctx->m_v32;
     A.e = ctx->e;

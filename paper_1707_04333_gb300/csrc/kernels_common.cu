@@ -12,7 +12,8 @@ namespace fetdpic {
 // with [*mu^-1] = 1/(mu0 A_f) folded into ecoef = s_f/(mu0 A_f).  The
 // fixed-point current is converted (unit = (q_ref/dt) 2^-shift per
 // instance), kept in j for reading, and cleared for the next step.  The dual
-// flux d += dt r accumulates for the Gauss-law check.
+// flux d += dt r accumulates for the Gauss-law check (d == NULL: checks off);
+// r (FP64) is stored for the FP64 SpMV, r32 for the FP32 one (either NULL).
 __global__ void k_curl_h(int E, const int2 *__restrict__ efac, const double2 *__restrict__ ecoef,
                          const int *__restrict__ einst, const double *__restrict__ unit,
                          const double *__restrict__ idt, const double *__restrict__ b,
@@ -30,10 +31,10 @@ __global__ void k_curl_h(int E, const int2 *__restrict__ efac, const double2 *__
     ifix[e] = 0ull;
     const double cur = (double)iv * unit[in];
     const double rv = h - cur;
-    r[e] = rv;
+    if (r) r[e] = rv;
     if (r32) r32[e] = (float)rv;
     j[e] = cur;
-    d[e] += idt[in] * rv;
+    if (d) d[e] += idt[in] * rv;
 }
 
 // e_free += (dt M) r: SpMV with the dt-scaled SPAI in sliced ELL (slices of
