@@ -23,6 +23,7 @@ import subprocess
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fetdpic_oracle.c")
@@ -323,6 +324,30 @@ class OracleSim:
         self.step_count += 1
         self.status = status
         return recs
+
+    def electrostatic_solve(self):
+        """Initial electrostatic field of the loaded charge (Gauss law, Eq. (semi.dis.div.2), with
+        e = -G phi): [*eps] restricted to free edges, G the node-to-edge gradient incidence
+        (G = -S~^T), phi = 0 on nodes of PEC edges; solves G^T [*eps] G phi = q on the other nodes
+        and adds e = -G phi to the edge unknowns; d = [*eps] e.  Returns phi."""
+        m = self.mesh
+        G = -m.div_dual().T.tocsr()                       # edges x nodes: +1 at the head, -1 at the tail
+        pec_nodes = np.unique(m.edge[m.edge_bnd == 1])
+        has_edge = np.zeros(m.nn, bool)
+        has_edge[m.edge.ravel()] = True
+        free_n = np.setdiff1d(np.nonzero(has_edge)[0], pec_nodes)
+        free_e = m.edge_bnd == 0
+        Gf = G[free_e][:, free_n]
+        Ef = self.star_eps[free_e][:, free_e]
+        K = (Gf.T @ Ef @ Gf).tocsc()
+        q = self.charge()
+        phi = np.zeros(m.nn)
+        phi[free_n] = spla.spsolve(K, q[free_n])
+        de = -(G @ phi)
+        de[~free_e] = 0.0
+        self.e = self.e + de
+        self.d = self.star_eps @ self.e
+        return phi
 
     def field_energy(self) -> float:
         """eps-energy e.[*eps].e/2 + mu-energy b.[*mu^-1].b/2 (FP64)."""
