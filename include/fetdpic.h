@@ -225,6 +225,24 @@ int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *rec);
  * Any output may be NULL. */
 int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double *dgl_max, double *energy);
 
+/* Initial electrostatic field of a non-neutral load.  The discrete Gauss law
+ * (Eq. (semi.dis.div.2)) asks S~ [*eps] e = q of the field; a load whose
+ * charges do not cancel needs a starting e that carries them.  With the
+ * particles of instance `inst` as loaded by fetdpic_load_particles (before
+ * the first step), computes their nodal charge q_i = sum Q lambda_i(r_p)
+ * (Eq. (scatter.charge.assign)), solves G^T [*eps] G phi = q on the nodes off
+ * the PEC walls (phi = 0 on them; G the node-to-edge incidence, G = -S~^T)
+ * by Jacobi-preconditioned conjugate gradients on the host in FP64 (relative
+ * residual <= 1e-14), adds e = -G phi to the instance's edge unknowns and
+ * restarts the dual flux d = [*eps] e.  From then on the instance's
+ * Gauss-law check (fetdpic_check) measures S~ d^n - q^n itself on the nodes
+ * off the PEC walls instead of its change since the first step (on wall
+ * nodes S~ d - q is the conductor's induced charge and is still compared
+ * with its first value); fetdpic_write_fields with an e reverts that.  *iterations and *residual (either may be NULL) report the solve.
+ * ESTATE after the first step or on a mesh without PEC walls; EMESH if the
+ * solve does not converge. */
+int fetdpic_solve_electrostatic(fetdpic_ctx *ctx, int inst, int *iterations, double *residual);
+
 /* Field probes, a diagnostic around the step: the paper reads its relativistic
  * Bernstein-mode spectra off E_x sampled along a line of the domain at every
  * time step, Fourier-transformed in space and time (Sec. III.C).  Registers

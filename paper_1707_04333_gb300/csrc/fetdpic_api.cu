@@ -92,6 +92,8 @@ struct fetdpic_ctx {
     long long *h_rp = nullptr; int *h_ci = nullptr; double *h_v = nullptr;
     bool q_prev_valid = false;                // q0 holds the charge of the current particle state
     bool g0_ready = false;
+    std::vector<char> gauss_abs;              // per instance: Gauss law checked absolutely (after the solve)
+    std::vector<std::vector<char>> abs_nodes; // per instance: nodes off the PEC walls (absolute reference 0)
     // reusable device scratch for host <-> device transfers of particle state
     void *xfer = nullptr; size_t xfer_bytes = 0;
 
@@ -206,6 +208,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
 
     // ---- host setup per instance
     ctx->mesh.resize(n_inst);
+    ctx->gauss_abs.assign(n_inst, 0);
+    ctx->abs_nodes.assign(n_inst, {});
     ctx->inst.assign(inst, inst + n_inst);
     ctx->cell_off.assign(n_inst + 1, 0);
     ctx->edge_off.assign(n_inst + 1, 0);
@@ -516,6 +520,19 @@ static void reset_gauss_reference(fetdpic_ctx *ctx)
     charge_now(ctx, ctx->q0);
     launch_dgl(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->qunit, ctx->d, ctx->q0, ctx->g0, 1,
                ctx->chk_out);
+    // after the electrostatic solve the reference is zero off the PEC walls: S~ d^n = q^n itself is
+    // checked there; on wall nodes S~ d - q is the conductor's induced charge and stays relative
+    for (size_t k = 0; k < ctx->gauss_abs.size(); ++k) {
+        if (!ctx->gauss_abs[k]) continue;
+        const int nn = ctx->mesh[k].nn;
+        std::vector<double> g(nn);
+        if (cudaMemcpyAsync(g.data(), ctx->g0 + ctx->node_off[k], sizeof(double) * nn, cudaMemcpyDeviceToHost,
+                            ctx->stream) != cudaSuccess || cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+            continue;
+        for (int n = 0; n < nn; ++n) if (ctx->abs_nodes[k][n]) g[n] = 0.0;
+        cudaMemcpyAsync(ctx->g0 + ctx->node_off[k], g.data(), sizeof(double) * nn, cudaMemcpyHostToDevice, ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+    }
     ctx->q_prev_valid = true;
     ctx->g0_ready = true;
 }
@@ -978,7 +995,62 @@ extern "C" int fetdpic_write_fields(fetdpic_ctx *ctx, int inst, const double *e,
         if (rc) return rc;
         CK(cudaStreamSynchronize(ctx->stream));
     }
-    if (e) reset_gauss_reference(ctx);
+    if (e) {
+        ctx->gauss_abs[inst] = 0;              // a caller's field need not satisfy Gauss's law
+        reset_gauss_reference(ctx);
+    }
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_solve_electrostatic(fetdpic_ctx *ctx, int inst, int *iterations, double *residual)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    if (ctx->steps_done > 0)
+        return ctx->fail(FETDPIC_ESTATE, "the electrostatic solve uses the loaded particles: call it before the first step");
+    const HostMesh &M = ctx->mesh[inst];
+    // nodal charge of the loaded particles, Eq. (scatter.charge.assign): q_i += Q lambda_i(r_p)
+    std::vector<double> q(M.nn, 0.0);
+    for (const auto &S : ctx->staged) {
+        if (S.inst != inst) continue;
+        for (size_t k = 0; k < S.cell.size(); ++k) {
+            double l[3];
+            host_lambdas(M, S.cell[k], S.x[k], S.y[k], l);
+            for (int m = 0; m < 3; ++m) q[M.rep[M.tri[3 * S.cell[k] + m]]] += S.q * l[m];
+        }
+    }
+    std::vector<double> de;
+    int it = 0;
+    double res = 0.0;
+    std::string msg;
+    int rc = electrostatic_solve(M, q, de, it, res, msg);
+    if (rc) return ctx->fail(rc, msg);
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::vector<double> ev(M.ne);
+    CK(cudaMemcpy(ev.data(), ctx->e + ctx->edge_off[inst], sizeof(double) * M.ne, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < M.ne; ++k) ev[k] += de[k];
+    rc = upload(ctx, ctx->e + ctx->edge_off[inst], ev.data(), ev.size());
+    if (rc) return rc;
+    std::vector<double> dv(M.ne, 0.0);
+    for (int k = 0; k < M.ne; ++k)
+        for (long long p = M.h_rp[k]; p < M.h_rp[k + 1]; ++p) dv[k] += M.h_v[p] * ev[M.h_ci[p]];
+    rc = upload(ctx, ctx->d + ctx->edge_off[inst], dv.data(), dv.size());
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->gauss_abs[inst] = 1;
+    auto &an = ctx->abs_nodes[inst];
+    an.assign(M.nn, 0);
+    {
+        std::vector<char> pec_node(M.nn, 0), free_node(M.nn, 0);
+        for (int k = 0; k < M.ne; ++k) {
+            char *t = M.pec[k] ? pec_node.data() : free_node.data();
+            t[M.edge[2 * k]] = t[M.edge[2 * k + 1]] = 1;
+        }
+        for (int n = 0; n < M.nn; ++n) an[n] = free_node[n] && !pec_node[n];
+    }
+    reset_gauss_reference(ctx);
+    if (iterations) *iterations = it;
+    if (residual) *residual = res;
     return FETDPIC_OK;
 }
 

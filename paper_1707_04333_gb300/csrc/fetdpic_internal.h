@@ -51,6 +51,13 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri,
 int build_hodge(HostMesh &M, double eps0, std::string &msg);
 int build_spai(HostMesh &M, int level, std::string &msg);
 
+// Initial electrostatic field of nodal charges q [nn] (node ids of the mesh;
+// images of periodic nodes carry none): solves G^T [*eps] G phi = q on the
+// nodes off the PEC walls (phi = 0 on them) by Jacobi-preconditioned
+// conjugate gradients and returns de = -G phi [ne] (0 on PEC edges).
+int electrostatic_solve(const HostMesh &M, const std::vector<double> &q, std::vector<double> &de,
+                        int &iterations, double &rel_residual, std::string &msg);
+
 // Same barycentric evaluation the kernels use (gradient form, no FMA).
 void host_lambdas(const HostMesh &M, int f, double x, double y, double *l);
 int host_locate(const HostMesh &M, double x, double y, int hint);

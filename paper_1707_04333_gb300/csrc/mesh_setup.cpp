@@ -178,6 +178,85 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
     return FETDPIC_OK;
 }
 
+int electrostatic_solve(const HostMesh &M, const std::vector<double> &q, std::vector<double> &de,
+                        int &iterations, double &rel_residual, std::string &msg)
+{
+    const int nn = M.nn, ne = M.ne;
+    if ((int)q.size() != nn) { msg = "charge size"; return FETDPIC_EINVAL; }
+    if (M.h_rp.empty()) { msg = "Hodge matrix not built"; return FETDPIC_ESTATE; }
+    // unknowns: nodes that bound a free edge and no PEC edge (images own no edge)
+    std::vector<char> has_free(nn, 0), on_pec(nn, 0);
+    for (int e = 0; e < ne; ++e) {
+        const int a = M.edge[2 * e], b = M.edge[2 * e + 1];
+        if (M.pec[e]) { on_pec[a] = on_pec[b] = 1; }
+        else { has_free[a] = has_free[b] = 1; }
+    }
+    std::vector<char> unk(nn);
+    bool any_pec = false;
+    for (int n = 0; n < nn; ++n) { unk[n] = has_free[n] && !on_pec[n]; any_pec = any_pec || on_pec[n]; }
+    if (!any_pec) { msg = "the electrostatic solve needs a PEC wall (the potential is fixed there)"; return FETDPIC_ESTATE; }
+    // K phi = G^T [*eps] (G phi) over free edges, phi = 0 off the unknowns
+    std::vector<double> g(ne), h(ne);
+    auto apply = [&](const std::vector<double> &phi, std::vector<double> &out) {
+        for (int e = 0; e < ne; ++e) g[e] = M.pec[e] ? 0.0 : phi[M.edge[2 * e + 1]] - phi[M.edge[2 * e]];
+        for (int e = 0; e < ne; ++e) {
+            double s = 0.0;
+            if (!M.pec[e])
+                for (long long k = M.h_rp[e]; k < M.h_rp[e + 1]; ++k) s += M.h_v[k] * g[M.h_ci[k]];
+            h[e] = s;
+        }
+        std::fill(out.begin(), out.end(), 0.0);
+        for (int e = 0; e < ne; ++e) {
+            out[M.edge[2 * e + 1]] += h[e];
+            out[M.edge[2 * e]] -= h[e];
+        }
+        for (int n = 0; n < nn; ++n) if (!unk[n]) out[n] = 0.0;
+    };
+    // Jacobi: diag K ~ sum over incident free edges of [*eps]_ee
+    std::vector<double> dg(nn, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        if (M.pec[e]) continue;
+        double dee = 0.0;
+        for (long long k = M.h_rp[e]; k < M.h_rp[e + 1]; ++k) if (M.h_ci[k] == e) dee = M.h_v[k];
+        dg[M.edge[2 * e]] += dee; dg[M.edge[2 * e + 1]] += dee;
+    }
+    std::vector<double> x(nn, 0.0), r(nn), z(nn), pv(nn), Ap(nn);
+    double bn = 0.0;
+    for (int n = 0; n < nn; ++n) { r[n] = unk[n] ? q[n] : 0.0; bn += r[n] * r[n]; }
+    bn = std::sqrt(bn);
+    iterations = 0; rel_residual = 0.0;
+    de.assign(ne, 0.0);
+    if (bn == 0.0) return FETDPIC_OK;
+    for (int n = 0; n < nn; ++n) z[n] = unk[n] && dg[n] > 0 ? r[n] / dg[n] : 0.0;
+    pv = z;
+    double rz = 0.0;
+    for (int n = 0; n < nn; ++n) rz += r[n] * z[n];
+    const int max_it = 20 * nn + 100;
+    double rn = bn;
+    for (int it = 1; it <= max_it; ++it) {
+        apply(pv, Ap);
+        double pAp = 0.0;
+        for (int n = 0; n < nn; ++n) pAp += pv[n] * Ap[n];
+        if (!(pAp > 0.0)) { msg = "electrostatic solve: matrix not positive definite"; return FETDPIC_EMESH; }
+        const double alpha = rz / pAp;
+        rn = 0.0;
+        for (int n = 0; n < nn; ++n) { x[n] += alpha * pv[n]; r[n] -= alpha * Ap[n]; rn += r[n] * r[n]; }
+        rn = std::sqrt(rn);
+        iterations = it;
+        if (rn <= 1e-14 * bn) break;
+        for (int n = 0; n < nn; ++n) z[n] = unk[n] && dg[n] > 0 ? r[n] / dg[n] : 0.0;
+        double rz2 = 0.0;
+        for (int n = 0; n < nn; ++n) rz2 += r[n] * z[n];
+        const double beta = rz2 / rz;
+        rz = rz2;
+        for (int n = 0; n < nn; ++n) pv[n] = z[n] + beta * pv[n];
+    }
+    rel_residual = rn / bn;
+    if (rel_residual > 1e-12) { msg = "electrostatic solve did not converge"; return FETDPIC_EMESH; }
+    for (int e = 0; e < ne; ++e) de[e] = M.pec[e] ? 0.0 : -(x[M.edge[2 * e + 1]] - x[M.edge[2 * e]]);
+    return FETDPIC_OK;
+}
+
 void host_lambdas(const HostMesh &M, int f, double x, double y, double *l)
 {
     for (int m = 0; m < 3; ++m) {

@@ -79,6 +79,7 @@ def lib():
             "fetdpic_info": (i32, [vp, i32, vp]),
             "fetdpic_read_edges": (i32, [vp, i32, vp]),
             "fetdpic_set_probes": (i32, [vp, i64, vp, vp, i64]),
+            "fetdpic_solve_electrostatic": (i32, [vp, i32, vp, vp]),
             "fetdpic_read_probes": (i32, [vp, vp, i64, vp, vp]),
             "fetdpic_read_spai": (i32, [vp, i32, vp, vp, vp, vp]),
             "fetdpic_stage_times": (i32, [vp, vp, vp]),
@@ -402,6 +403,12 @@ class Simulation:
 
     def read_fields(self, inst=0):
         return fetdpic_read(self.h, inst, species=None, fields=True)
+
+    def solve_electrostatic(self, inst=0):
+        """Initial field of the loaded charge (before the first step): (CG iterations, residual)."""
+        it, res = C.c_int(), C.c_double()
+        _check(self.h, lib().fetdpic_solve_electrostatic(self.h, inst, C.byref(it), C.byref(res)))
+        return it.value, res.value
 
     def set_probes(self, xy, inst=None, capacity=4096):
         fetdpic_set_probes(self.h, xy, inst, capacity)
