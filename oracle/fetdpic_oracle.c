@@ -489,6 +489,12 @@ typedef struct {
     double ext_ex, ext_ey, ext_bz;
     int pusher;
     int max_cross;
+    /* applied fields that vary in space and time (a synchrocyclotron's magnet
+     * and RF gap, Sec. III.A): in triangle f the external E is
+     * (ext_amp * ext_w[2f]) * (ext_ex, ext_ey) and the external B_z is
+     * ext_w[2f+1] * ext_bz; ext_w NULL = weights 1 */
+    const double *ext_w;
+    double ext_amp;
 } ora_step_params;
 
 /* Current of one sub-segment inside triangle f, Eq. (I.assign):
@@ -536,9 +542,11 @@ int ora_particles(const ora_mesh *M, const ora_step_params *P,
             E[0] += se * wx;
             E[1] += se * wy;
         }
-        E[0] += P->ext_ex;
-        E[1] += P->ext_ey;
-        double B[3] = { 0.0, 0.0, (b_new[f] + b_old[f]) * M->inv2A[f] + P->ext_bz };
+        const double we = P->ext_w ? P->ext_w[2 * f] : 1.0, wb = P->ext_w ? P->ext_w[2 * f + 1] : 1.0;
+        const double se = P->ext_amp * we;
+        E[0] += se * P->ext_ex;
+        E[1] += se * P->ext_ey;
+        double B[3] = { 0.0, 0.0, (b_new[f] + b_old[f]) * M->inv2A[f] + wb * P->ext_bz };
         double u[3] = { ux[p], uy[p], uz[p] };
         double g = push(P->pusher, alpha, P->c, ic2, E, B, u);
         double ig = 1.0 / g;

@@ -67,7 +67,7 @@ class _MeshC(C.Structure):
 class _StepC(C.Structure):
     _fields_ = [("dt", C.c_double), ("c", C.c_double), ("q", C.c_double), ("m", C.c_double),
                 ("ext_ex", C.c_double), ("ext_ey", C.c_double), ("ext_bz", C.c_double),
-                ("pusher", C.c_int), ("max_cross", C.c_int)]
+                ("pusher", C.c_int), ("max_cross", C.c_int), ("ext_w", C.c_void_p), ("ext_amp", C.c_double)]
 
 
 def _p(a):
@@ -265,6 +265,10 @@ class OracleSim:
         self.b_half = self.b.copy()    # b^{n+1/2} of the last step
         self.species = []
         self.step_count = 0
+        # applied fields varying in space and time: per-triangle weights (E, B) of ext and an
+        # amplitude multiplying the external E (None = weights 1)
+        self.ext_profile = None
+        self.ext_amp = 1.0
 
     def load(self, q, m_, x, u, hint=None, cell=None):
         """Add a species; `cell` (if given) is taken as the host triangle of each point as is."""
@@ -301,8 +305,9 @@ class OracleSim:
         status = 0
         for s in self.species:
             n = len(s["x"])
+            prof = None if self.ext_profile is None else np.ascontiguousarray(self.ext_profile, np.float64)
             P = _StepC(self.dt, self.c, s["q"], s["m"], self.ext[0], self.ext[1], self.ext[2], pid,
-                       self.max_cross)
+                       self.max_cross, None if prof is None else _p(prof), float(self.ext_amp))
             cnt = np.zeros(n, np.int32) if record else None
             rec = np.full((n, max(record, 1)), -(1 << 30), np.int32) if record else None
             st = lib().ora_particles(m.cs, C.byref(P), _p(self.e), _p(self.b), _p(b_new), n,

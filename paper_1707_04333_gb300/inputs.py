@@ -55,6 +55,8 @@ class Workload:
     e0: tuple = (0.0, 0.0)  # uniform initial E (projected onto free-edge DoFs)
     ext: tuple = (0.0, 0.0, 0.0)  # external uniform (E_x, E_y, B_z) added at the particle
     pusher: str = "boris"
+    # per-triangle weights [F,2] of the external E and B_z (None = 1 everywhere)
+    ext_profile: object = None
 
     @property
     def n_particles(self) -> int:
@@ -246,3 +248,54 @@ def batched_pair_plasmas(n_inst: int = 64, seed: int = 5, f_range=(5_000, 200_00
         kT = math.exp(math.log(0.01) + (math.log(0.3) - math.log(0.01)) * ((k * 37) % n_inst) / max(1, n_inst - 1))
         out.append(pair_plasma(side_n, ppc, kT, wc_wp, seed=seed * 1000 + k))
     return out
+
+
+def synchrocyclotron(n: int = 100, v0: float = 1e7, radius: float = 0.02, e0: float = 2e5,
+                     gap: float = 0.02, steps_per_turn: int = 200) -> Workload:
+    """The paper's synchrocyclotron case (Sec. III.A): a 1 m x 1 m square, B_z from the magnet
+    everywhere (its poles cover the gap too) and an RF field E_x in a vertical gap strip
+    |x - 0.5| < gap/2.
+
+    B_z = m0 v0 / (|q| r) for an initial orbit radius r (2.84281e-3 T for v0 = 1e7 m/s, r = 0.02 m,
+    as printed), E_x amplitude e0, one electron injected at (0.5 + r, 0.5) moving along +y
+    (counter-clockwise about (0.5, 0.5)).  Structured mesh of n x n cells (jitter 0) so the gap
+    edges are mesh lines; dt = (2 pi / omega_c) / steps_per_turn.  The external E carries weight 1
+    in the gap and 0 elsewhere, the external B weight 1 everywhere (Workload.ext_profile); the RF
+    time dependence is an amplitude set every step (RFDrive)."""
+    mesh = jittered_delaunay(n, n, 1.0, 1.0, 0.0, seed=0)
+    t = mesh.triangles
+    xc = mesh.nodes[t, 0].mean(axis=1)
+    in_gap = np.abs(xc - 0.5) < 0.5 * gap
+    profile = np.stack([in_gap, np.ones_like(in_gap)], axis=1).astype(np.float64)
+    b0 = M_E * v0 / (Q_E * radius)
+    wc = Q_E * b0 / M_E
+    dt = 2.0 * math.pi / wc / steps_per_turn
+    g = 1.0 / math.sqrt(1.0 - (v0 / C_LIGHT) ** 2)
+    x = np.array([[0.5 + radius, 0.5]])
+    u = np.array([[0.0, g * v0]])
+    el = Species(-Q_E, M_E, x, u, np.full(1, -1, np.int32))
+    return Workload(f"synchrocyclotron-{len(t)}tri", mesh, [el], dt, b0=0.0, ext=(e0, 0.0, b0),
+                    pusher="boris", ext_profile=profile)
+
+
+class RFDrive:
+    """Phase of the synchrocyclotron's RF gap field, E_x = e0 sin(phi).  The electron (counter-
+    clockwise in B_z > 0) crosses the gap moving -x at the top of its orbit a quarter turn after
+    injection and +x at the bottom, so sin(phi) with phi(0) = 0 accelerates it at both crossings
+    while the drive keeps pace.  Each step phi advances by omega dt: omega = omega_c / gamma
+    (synchronized: the paper's f = qB / (2 pi gamma m0), gamma of the electron after the step) or
+    the constant omega_c (f = 79.6 MHz for the printed field)."""
+
+    def __init__(self, b0: float, dt: float, synchronized: bool):
+        self.wc = Q_E * b0 / M_E
+        self.dt = dt
+        self.synchronized = synchronized
+        self.phi = 0.0
+
+    def amplitude(self) -> float:
+        return math.sin(self.phi)
+
+    def advance(self, u) -> None:
+        u = np.asarray(u, np.float64).reshape(-1)
+        gamma = math.sqrt(1.0 + (u[0] * u[0] + u[1] * u[1]) / (C_LIGHT * C_LIGHT))
+        self.phi += (self.wc / gamma if self.synchronized else self.wc) * self.dt
