@@ -225,6 +225,24 @@ int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *rec);
  * Any output may be NULL. */
 int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double *dgl_max, double *energy);
 
+/* Applied fields that vary in space and time (the synchrocyclotron of
+ * Sec. III.A: a magnet over the whole region and an RF field in a gap strip,
+ * its frequency following the electrons).  The instance's uniform external
+ * fields (ext_ex, ext_ey, ext_bz of fetdpic_instance) act on a particle in
+ * triangle f as E = a w_E[f] (ext_ex, ext_ey) and B_z = w_B[f] ext_bz, with
+ * a the instance's amplitude (1 until set).
+ *
+ * fetdpic_set_external_profile: w [n_tri][2] = (w_E, w_B) per triangle of
+ * instance `inst` (host array, copied); NULL = all 1.  The first call
+ * allocates the weights for all instances (1 elsewhere) and re-captures step
+ * graphs.  EINVAL on a non-finite weight.
+ *
+ * fetdpic_set_external_amplitude: a for the steps enqueued after this call
+ * (stream-ordered; steps replayed from graphs see it too).  Returns once the
+ * value is on the device.  EINVAL on a non-finite a. */
+int fetdpic_set_external_profile(fetdpic_ctx *ctx, int inst, const double *w);
+int fetdpic_set_external_amplitude(fetdpic_ctx *ctx, int inst, double amplitude);
+
 /* Initial electrostatic field of a non-neutral load.  The discrete Gauss law
  * (Eq. (semi.dis.div.2)) asks S~ [*eps] e = q of the field; a load whose
  * charges do not cancel needs a starting e that carries them.  With the

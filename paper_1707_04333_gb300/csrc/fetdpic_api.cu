@@ -73,6 +73,12 @@ struct fetdpic_ctx {
     short *chunk_sp = nullptr;               // species of each 32-particle chunk
     signed char *tshift = nullptr;           // periodic shift codes (FP64 walk), NULL without periodic walls
     double2 *period = nullptr;               // per instance
+    // applied fields: per-instance (E_x, E_y, B_z, 0) and amplitude of E, per-triangle weights
+    ExtField *ext_dev = nullptr;
+    double *ext_amp = nullptr;
+    double2 *extw = nullptr;                 // NULL until a profile is set
+    int *face_inst = nullptr;                // FP32: instance of each triangle
+    bool ext_on = false;                     // FP32: fold applied fields into the field record
     int *hist = nullptr, *hoff = nullptr, *scan_tmp = nullptr; long long hist_n = 0;
     long long *pad_adj = nullptr;
     int *rec_cnt = nullptr, *rec = nullptr;
@@ -409,6 +415,9 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             ctx->tshift = ctx->alloc<signed char>(3 * (size_t)ctx->F);
             ctx->period = ctx->alloc<double2>(n_inst);
         }
+        ctx->ext_dev = ctx->alloc<ExtField>(n_inst);
+        ctx->ext_amp = ctx->alloc<double>(n_inst);
+        if (P.precision == FETDPIC_FP32) ctx->face_inst = ctx->alloc<int>(ctx->F);
         ctx->m_soff = ctx->alloc<long long>(soff.size());
         ctx->m_row = ctx->alloc<int>(mrow.size());
         ctx->m_ci = ctx->alloc<int>(sci.size());
@@ -462,6 +471,22 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (any_periodic) {
         rc = rc ? rc : upload(ctx, ctx->tshift, tsh.data(), tsh.size());
         rc = rc ? rc : upload(ctx, ctx->period, per.data(), per.size());
+    }
+    {
+        std::vector<ExtField> ex(n_inst);
+        std::vector<double> amp(n_inst, 1.0);
+        for (int k = 0; k < n_inst; ++k) {
+            ex[k] = ExtField{inst[k].ext_ex, inst[k].ext_ey, inst[k].ext_bz, 0.0};
+            ctx->ext_on = ctx->ext_on || inst[k].ext_ex != 0.0 || inst[k].ext_ey != 0.0 || inst[k].ext_bz != 0.0;
+        }
+        rc = rc ? rc : upload(ctx, ctx->ext_dev, ex.data(), ex.size());
+        rc = rc ? rc : upload(ctx, ctx->ext_amp, amp.data(), amp.size());
+        if (ctx->face_inst) {
+            std::vector<int> fi(ctx->F);
+            for (int k = 0; k < n_inst; ++k)
+                for (int f = ctx->cell_off[k]; f < ctx->cell_off[k + 1]; ++f) fi[f] = k;
+            rc = rc ? rc : upload(ctx, ctx->face_inst, fi.data(), fi.size());
+        }
     }
     rc = rc ? rc : upload(ctx, ctx->m_soff, soff.data(), soff.size());
     rc = rc ? rc : upload(ctx, ctx->m_row, mrow.data(), mrow.size());
@@ -611,7 +636,8 @@ static int finalize(fetdpic_ctx *ctx)
     for (int s = 0; s < ns; ++s) {
         const Species &D = ctx->sp[s];
         Sp32 &T = s32[s];
-        T.kappa = D.kappa; T.xe_x = D.xe_x; T.xe_y = D.xe_y; T.xb = D.xb;
+        // the FP32 path takes the applied fields from the per-triangle field record
+        T.kappa = D.kappa; T.xe_x = 0.0f; T.xe_y = 0.0f; T.xb = 0.0f;
         T.wfix = (float)D.wfix;
         T.inst = D.inst; T.edge_off = ctx->edge_off[D.inst]; T.pad = 0;
     }
@@ -710,6 +736,7 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
     a.edge_off = ctx->edge_off_dev;
     a.nblocks = ctx->nblocks; a.block = ctx->block;
     a.tshift = ctx->tshift; a.period = ctx->period;
+    a.extw = ctx->extw; a.ext_amp = ctx->ext_amp;
     return a;
 }
 
@@ -781,8 +808,15 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     long long launches = 0;
     const bool f32 = ctx->p.precision == FETDPIC_FP32;
     if (timed) mark(ctx, -1);
-    if (f32) launch_faraday32(ctx->stream, ctx->F, ctx->cst32, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
-                              (float)(0.5 / (ctx->p.c * ctx->p.c)));
+    if (f32) {
+        Ext32 x{};
+        if (ctx->ext_on) {
+            x.finst = ctx->face_inst; x.ext = ctx->ext_dev; x.amp = ctx->ext_amp; x.extw = ctx->extw;
+            x.half_over_c = 0.5 / ctx->p.c;
+        }
+        launch_faraday32(ctx->stream, ctx->F, ctx->cst32, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
+                         (float)(0.5 / (ctx->p.c * ctx->p.c)), x);
+    }
     else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
     launches += ctx->F > 0;
     if (timed) mark(ctx, 0);
@@ -1153,6 +1187,44 @@ extern "C" int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6])
 }
 
 static void drop_graphs(fetdpic_ctx *ctx);
+
+extern "C" int fetdpic_set_external_profile(fetdpic_ctx *ctx, int inst, const double *w)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    const int nf = ctx->mesh[inst].nf;
+    std::vector<double2> wv(nf, make_double2(1.0, 1.0));
+    if (w)
+        for (int f = 0; f < nf; ++f) {
+            if (!std::isfinite(w[2 * f]) || !std::isfinite(w[2 * f + 1]))
+                return ctx->fail(FETDPIC_EINVAL, "non-finite applied-field weight");
+            wv[f] = make_double2(w[2 * f], w[2 * f + 1]);
+        }
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (!ctx->extw) {
+        try { ctx->extw = ctx->alloc<double2>(ctx->F); } catch (const std::bad_alloc &) { return FETDPIC_ENOMEM; }
+        std::vector<double2> ones(ctx->F, make_double2(1.0, 1.0));
+        int rc = upload(ctx, ctx->extw, ones.data(), ones.size());
+        if (rc) return rc;
+        drop_graphs(ctx);                      // captured steps hold no weights
+    }
+    int rc = upload(ctx, ctx->extw + ctx->cell_off[inst], wv.data(), wv.size());
+    if (rc) return rc;
+    if (!ctx->ext_on) { ctx->ext_on = true; drop_graphs(ctx); }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_set_external_amplitude(fetdpic_ctx *ctx, int inst, double amplitude)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    if (!std::isfinite(amplitude)) return ctx->fail(FETDPIC_EINVAL, "non-finite amplitude");
+    CK(cudaSetDevice(ctx->device));
+    // stream-ordered: steps enqueued before see the old value, later ones the new
+    CK(cudaMemcpyAsync(ctx->ext_amp + inst, &amplitude, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return FETDPIC_OK;
+}
 
 extern "C" int fetdpic_set_probes(fetdpic_ctx *ctx, long long n, const int *inst, const double *xy,
                                   long long capacity)

@@ -140,6 +140,8 @@ struct StepArgs64 {
     long long nblocks; int block;
     const signed char *tshift;              // [F][3] periodic shift codes; NULL = no periodic walls
     const double2 *period;                  // per instance (tx, ty)
+    const double2 *extw;                    // [F] weights (E, B) of the applied fields; NULL = 1
+    const double *ext_amp;                  // per instance: amplitude of the applied E
 };
 
 struct StepArgs32 {
@@ -158,8 +160,13 @@ struct StepArgs32 {
 
 void launch_faraday64(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
                       double *b, Rec64 *rec);
+// Applied fields folded into the FP32 field record (ext == NULL: none): per
+// instance (E_x, E_y, B_z, 0) times the amplitude (E) and the per-triangle
+// weights extw (NULL = 1); finst = instance of each triangle.
+struct __align__(16) ExtField { double ex, ey, bz, pad; };
+struct Ext32 { const int *finst; const ExtField *ext; const double *amp; const double2 *extw; double half_over_c; };
 void launch_faraday32(cudaStream_t st, int F, const Cst32 *cst, const double2 *dtinv, const double *e,
-                      double *b, Rec32 *rec, float inv2c2);
+                      double *b, Rec32 *rec, float inv2c2, const Ext32 &x);
 void launch_particles64(cudaStream_t st, int pusher, const StepArgs64 &a);
 void launch_particles32(cudaStream_t st, int pusher, const StepArgs32 &a);
 

@@ -21,10 +21,11 @@ namespace fetdpic {
 // as dt/(2c) V_n = (s_{n-1} e_{n-1} G_{n+1} - s_{n+1} e_{n+1} G_{n-1}) / (2c^2)
 // (G = c dt grad l), so that q/m times it is alpha E / c; B_z^n stored as
 // (dt/2) B_z = (dt/2) (b^{n+1/2} + b^{n-1/2}) / (2A).
+template <bool EXT>
 __global__ void __launch_bounds__(256) k_faraday32(int F, const Cst32 *__restrict__ cst,
                                                    const double2 *__restrict__ dtinv,
                                                    const double *__restrict__ e, double *__restrict__ b,
-                                                   Rec32 *__restrict__ rec, float inv2c2)
+                                                   Rec32 *__restrict__ rec, float inv2c2, Ext32 x)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
@@ -50,17 +51,33 @@ __global__ void __launch_bounds__(256) k_faraday32(int F, const Cst32 *__restric
         r.v[2 * n] = s[nm] * G[2 * np] - s[np] * G[2 * nm];
         r.v[2 * n + 1] = s[nm] * G[2 * np + 1] - s[np] * G[2 * nm + 1];
     }
-    r.bz = (float)(0.5 * di.x * ((bn + bo) * di.y));
+    double bfield = (bn + bo) * di.y;
+    if (EXT) {
+        // a uniform applied E adds the same value to every node coefficient (sum of lambdas = 1)
+        const int k = x.finst[f];
+        const ExtField X = x.ext[k];
+        double we = 1.0, wb = 1.0;
+        if (x.extw) { const double2 wv = x.extw[f]; we = wv.x; wb = wv.y; }
+        const double sa = x.amp[k] * we * di.x * x.half_over_c;
+        const float ax = (float)(sa * X.ex), ay = (float)(sa * X.ey);
+#pragma unroll
+        for (int n = 0; n < 3; ++n) { r.v[2 * n] += ax; r.v[2 * n + 1] += ay; }
+        bfield += wb * X.bz;                         // B_z = (b^{n+1/2} + b^{n-1/2}) / (2A) + B_ext
+    }
+    r.bz = (float)(0.5 * di.x * bfield);
     float4 *rp = reinterpret_cast<float4 *>(rec + f);
     rp[0] = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
     rp[1] = make_float4(r.v[4], r.v[5], r.bz, __int_as_float(ew[0]));
 }
 
 void launch_faraday32(cudaStream_t st, int F, const Cst32 *cst, const double2 *dtinv, const double *e,
-                      double *b, Rec32 *rec, float inv2c2)
+                      double *b, Rec32 *rec, float inv2c2, const Ext32 &x)
 {
     if (F <= 0) return;
-    k_faraday32<<<(F + 255) / 256, 256, 0, st>>>(F, cst, dtinv, e, b, rec, inv2c2);
+    if (x.ext)
+        k_faraday32<true><<<(F + 255) / 256, 256, 0, st>>>(F, cst, dtinv, e, b, rec, inv2c2, x);
+    else
+        k_faraday32<false><<<(F + 255) / 256, 256, 0, st>>>(F, cst, dtinv, e, b, rec, inv2c2, x);
 }
 
 // --------------------------------------------------------------- pushers

@@ -196,9 +196,13 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
             Ex = Ex + R.se[m] * wx;
             Ey = Ey + R.se[m] * wy;
         }
-        Ex = Ex + S.ext_ex;
-        Ey = Ey + S.ext_ey;
-        const double Bz = R.bz + S.ext_bz;
+        // applied fields: (amplitude x E weight) E_ext, B weight x B_ext in this triangle
+        double we = 1.0, wb = 1.0;
+        if (a.extw) { const double2 wv = a.extw[f]; we = wv.x; wb = wv.y; }
+        const double sa = a.ext_amp[S.inst] * we;
+        Ex = Ex + sa * S.ext_ex;
+        Ey = Ey + sa * S.ext_ey;
+        const double Bz = R.bz + wb * S.ext_bz;
         const Push u = push64<PUSHER>(ux, uy, Ex, Ey, Bz, S.alpha, S.c, S.ic2);
         ux = u.ux; uy = u.uy;
         if (!isfinite(u.g) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.status, (unsigned)ST_NONFINITE);

@@ -80,6 +80,8 @@ def lib():
             "fetdpic_read_edges": (i32, [vp, i32, vp]),
             "fetdpic_set_probes": (i32, [vp, i64, vp, vp, i64]),
             "fetdpic_solve_electrostatic": (i32, [vp, i32, vp, vp]),
+            "fetdpic_set_external_profile": (i32, [vp, i32, vp]),
+            "fetdpic_set_external_amplitude": (i32, [vp, i32, dp]),
             "fetdpic_read_probes": (i32, [vp, vp, i64, vp, vp]),
             "fetdpic_read_spai": (i32, [vp, i32, vp, vp, vp, vp]),
             "fetdpic_stage_times": (i32, [vp, vp, vp]),
@@ -343,6 +345,9 @@ class Simulation:
             insts.append(I)
         self.params = p
         self.h = fetdpic_create(p, insts)
+        for k, w in enumerate(self.workloads):
+            if getattr(w, "ext_profile", None) is not None:
+                self.set_external_profile(w.ext_profile, k)
         self.species = []          # (instance, species id, n)
         self.record_walk = record_walk
 
@@ -403,6 +408,19 @@ class Simulation:
 
     def read_fields(self, inst=0):
         return fetdpic_read(self.h, inst, species=None, fields=True)
+
+    def set_external_profile(self, w, inst=0):
+        """Per-triangle weights (E, B) [n_tri][2] of the instance's applied fields (None = 1)."""
+        if w is None:
+            _check(self.h, lib().fetdpic_set_external_profile(self.h, inst, None))
+            return self
+        w = np.ascontiguousarray(w, np.float64).reshape(-1, 2)
+        _check(self.h, lib().fetdpic_set_external_profile(self.h, inst, _ptr(w)))
+        return self
+
+    def set_external_amplitude(self, a, inst=0):
+        _check(self.h, lib().fetdpic_set_external_amplitude(self.h, inst, float(a)))
+        return self
 
     def solve_electrostatic(self, inst=0):
         """Initial field of the loaded charge (before the first step): (CG iterations, residual)."""

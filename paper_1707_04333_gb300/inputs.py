@@ -251,7 +251,7 @@ def batched_pair_plasmas(n_inst: int = 64, seed: int = 5, f_range=(5_000, 200_00
 
 
 def synchrocyclotron(n: int = 100, v0: float = 1e7, radius: float = 0.02, e0: float = 2e5,
-                     gap: float = 0.02, steps_per_turn: int = 200) -> Workload:
+                     gap: float = 0.02, steps_per_turn: int = 2000, courant: float = 0.2) -> Workload:
     """The paper's synchrocyclotron case (Sec. III.A): a 1 m x 1 m square, B_z from the magnet
     everywhere (its poles cover the gap too) and an RF field E_x in a vertical gap strip
     |x - 0.5| < gap/2.
@@ -259,7 +259,8 @@ def synchrocyclotron(n: int = 100, v0: float = 1e7, radius: float = 0.02, e0: fl
     B_z = m0 v0 / (|q| r) for an initial orbit radius r (2.84281e-3 T for v0 = 1e7 m/s, r = 0.02 m,
     as printed), E_x amplitude e0, one electron injected at (0.5 + r, 0.5) moving along +y
     (counter-clockwise about (0.5, 0.5)).  Structured mesh of n x n cells (jitter 0) so the gap
-    edges are mesh lines; dt = (2 pi / omega_c) / steps_per_turn.  The external E carries weight 1
+    edges are mesh lines; dt = min((2 pi / omega_c) / steps_per_turn, courant h_min / c), the second
+    bound keeping the explicit field update stable.  The external E carries weight 1
     in the gap and 0 elsewhere, the external B weight 1 everywhere (Workload.ext_profile); the RF
     time dependence is an amplitude set every step (RFDrive)."""
     mesh = jittered_delaunay(n, n, 1.0, 1.0, 0.0, seed=0)
@@ -269,12 +270,14 @@ def synchrocyclotron(n: int = 100, v0: float = 1e7, radius: float = 0.02, e0: fl
     profile = np.stack([in_gap, np.ones_like(in_gap)], axis=1).astype(np.float64)
     b0 = M_E * v0 / (Q_E * radius)
     wc = Q_E * b0 / M_E
-    dt = 2.0 * math.pi / wc / steps_per_turn
+    p = mesh.nodes
+    el = np.concatenate([np.linalg.norm(p[t[:, a]] - p[t[:, b]], axis=1) for a, b in ((0, 1), (1, 2), (2, 0))])
+    dt = min(2.0 * math.pi / wc / steps_per_turn, courant * el.min() / C_LIGHT)
     g = 1.0 / math.sqrt(1.0 - (v0 / C_LIGHT) ** 2)
     x = np.array([[0.5 + radius, 0.5]])
     u = np.array([[0.0, g * v0]])
-    el = Species(-Q_E, M_E, x, u, np.full(1, -1, np.int32))
-    return Workload(f"synchrocyclotron-{len(t)}tri", mesh, [el], dt, b0=0.0, ext=(e0, 0.0, b0),
+    electron = Species(-Q_E, M_E, x, u, np.full(1, -1, np.int32))
+    return Workload(f"synchrocyclotron-{len(t)}tri", mesh, [electron], dt, b0=0.0, ext=(e0, 0.0, b0),
                     pusher="boris", ext_profile=profile)
 
 

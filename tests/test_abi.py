@@ -42,4 +42,6 @@ def test_invalid_arguments_rejected_without_gpu(libmod):
     assert L.fetdpic_set_probes(None, 0, None, None, 0) == libmod.EINVAL
     assert L.fetdpic_read_probes(None, None, 0, None, None) == libmod.EINVAL
     assert L.fetdpic_solve_electrostatic(None, 0, None, None) == libmod.EINVAL
+    assert L.fetdpic_set_external_profile(None, 0, None) == libmod.EINVAL
+    assert L.fetdpic_set_external_amplitude(None, 0, 1.0) == libmod.EINVAL
     assert L.fetdpic_last_error(None) == b"null context"

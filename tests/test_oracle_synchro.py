@@ -62,8 +62,8 @@ def test_static_gap_energy_gain(oracle_mod):
     assert abs(s["y"][0] - 0.5) < 1e-12 and abs(s["uy"][0]) == 0.0
 
 
-def _run_synchro(oracle_mod, synchronized, steps, steps_per_turn=1000):
-    w = inputs.synchrocyclotron(n=100, steps_per_turn=steps_per_turn)
+def _run_synchro(oracle_mod, synchronized, steps):
+    w = inputs.synchrocyclotron(n=100)
     sim = _sim(oracle_mod, w, fields=False)
     sim.ext_profile = w.ext_profile
     drive = inputs.RFDrive(w.ext[2], w.dt, synchronized)
@@ -86,7 +86,7 @@ def test_synchronised_drive_accelerates_every_crossing(oracle_mod):
     over 12 turns, by at most the work |q| E w = 4 keV of a crossing at the crest (plus the field
     the start-of-step triangle applies over at most one step beyond each gap edge) and by at least
     60 % of it (the transit-time factor of the sine over the crossing)."""
-    speed, kin, x, w = _run_synchro(oracle_mod, True, 12000)
+    speed, kin, x, w = _run_synchro(oracle_mod, True, 24000)
     in_gap = np.abs(x - 0.5) < 0.01
     edges = np.flatnonzero(np.diff(in_gap.astype(int)) == -1)     # steps where a crossing ends
     assert len(edges) >= 22
@@ -103,9 +103,9 @@ def test_unsynchronised_drive_falls_out_of_phase(oracle_mod):
     """Constant RF frequency (the rest-mass cyclotron frequency, 79.6 MHz for the printed field):
     the relativistic mass increase slips the phase; the electron first gains and then loses
     speed, as in the paper's comparison of velocity magnitudes."""
-    speed, kin, x, w = _run_synchro(oracle_mod, False, 12000)
+    speed, kin, x, w = _run_synchro(oracle_mod, False, 24000)
     k = int(np.argmax(speed))
-    assert 1000 < k < 11000
+    assert 2000 < k < 22000
     assert speed[-1] < 0.8 * speed[k]
     wc = QE * w.ext[2] / ME
     assert abs(wc / (2 * math.pi) / 1e6 - 79.6) < 0.05
