@@ -362,7 +362,7 @@ def main():
     if not args.no_fp64:
         k64 = args.fp64_steps or min(args.steps, 100)
         sim64, ms64, st64, l64, pb64, np64 = timed_run("fp64", k64, min(args.warmup, 3), stages=True,
-                                                       graphs=False, tuned=(3, sim.tuned[1]))
+                                                       graphs=False, tuned=(3, sim_tuned[1]))
         if world > 1:
             t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
