@@ -193,11 +193,20 @@ __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *_
     const long long c0 = w * SC_CHUNKS;
     int cc[SC_CHUNKS], slot[SC_CHUNKS], sid[SC_CHUNKS], base[SC_CHUNKS], rank[SC_CHUNKS];
     unsigned peers[SC_CHUNKS];
+    // the payload is loaded with the keys, so its DRAM latency overlaps the cursor atomics
+    int idv[SC_CHUNKS];
+    T v0[SC_CHUNKS], v1[SC_CHUNKS], v2[SC_CHUNKS], v3[SC_CHUNKS];
 #pragma unroll
     for (int k = 0; k < SC_CHUNKS; ++k) {
         const long long ch = c0 + k;
         cc[k] = -1; sid[k] = 0;
-        if (ch < nchunks) { cc[k] = cell[ch * 32 + lane]; sid[k] = chunk_sp[ch]; }
+        if (ch < nchunks) {
+            const long long p = ch * 32 + lane;
+            cc[k] = cell[p]; sid[k] = chunk_sp[ch];
+            idv[k] = id[p];
+            v0[k] = ((const T *)f0)[p]; v1[k] = ((const T *)f1)[p];
+            v2[k] = ((const T *)f2)[p]; v3[k] = ((const T *)f3)[p];
+        }
     }
 #pragma unroll
     for (int k = 0; k < SC_CHUNKS; ++k) {
@@ -212,14 +221,13 @@ __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *_
         const int leader = __ffs(peers[k]) - 1;
         const int b = __shfl_sync(0xffffffffu, base[k], leader);
         if (slot[k] < 0) continue;
-        const long long p = (c0 + k) * 32 + lane;
         const long long q = (long long)(b + rank[k]) + pad_adj[sid[k]];
         cell_o[q] = cc[k];
-        id_o[q] = id[p];
-        ((T *)g0)[q] = ((const T *)f0)[p];
-        ((T *)g1)[q] = ((const T *)f1)[p];
-        ((T *)g2)[q] = ((const T *)f2)[p];
-        ((T *)g3)[q] = ((const T *)f3)[p];
+        id_o[q] = idv[k];
+        ((T *)g0)[q] = v0[k];
+        ((T *)g1)[q] = v1[k];
+        ((T *)g2)[q] = v2[k];
+        ((T *)g3)[q] = v3[k];
     }
 }
 
