@@ -164,8 +164,12 @@ int fetdpic_load_particles(fetdpic_ctx *ctx, int inst, double q, double m, long 
  * arrays: x [n][2], u [n][2], cell [n] (instance-local triangle of each point,
  * e.g. from a previous fetdpic_read; NULL = locate again on the host).  With
  * `cell` the arrays are copied to the device as they are (fastest from
- * page-locked memory) and converted there.  Used for checkpoint/restart and
- * for end-to-end runs that stream the particle state from the host. */
+ * page-locked memory) and converted there, asynchronously on the stream: the
+ * host buffers must stay valid until the next fetdpic_sync or read, and a
+ * triangle index outside the instance's mesh is found on the device (that
+ * particle is dropped) and reported as FETDPIC_EINVAL by the next
+ * fetdpic_sync or fetdpic_read.  Used for checkpoint/restart and for
+ * end-to-end runs that stream the particle state from the host. */
 int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const double *x, const double *u, const int *cell);
 
 /* Overwrite the fields of instance `inst`: e [n_edges] (e^n, PEC entries are

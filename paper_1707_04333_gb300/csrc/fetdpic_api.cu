@@ -183,6 +183,9 @@ static int map_status(fetdpic_ctx *ctx, unsigned st)
     if (st & ST_WALK) return ctx->fail(FETDPIC_EWALK, "a particle crossed more than max_crossings edges in one step");
     if (st & ST_NONFINITE) return ctx->fail(FETDPIC_ENONFINITE, "non-finite momentum or Lorentz factor");
     if (st & ST_TIMEOUT) return ctx->fail(FETDPIC_ETIMEOUT, "a bounded wait for staged particle data gave up");
+    if (st & ST_BADCELL)
+        return ctx->fail(FETDPIC_EINVAL, "fetdpic_write_particles was given a triangle outside the mesh; "
+                                         "those particles were dropped");
     if (st) return ctx->fail(FETDPIC_EMESH, "device status " + std::to_string(st));
     return FETDPIC_OK;
 }
@@ -986,10 +989,8 @@ extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const doub
             if (located[k] < 0) return ctx->fail(FETDPIC_EOUTSIDE, "particle outside the mesh");
         }
         cl = located.data();
-    } else {
-        for (long long k = 0; k < D.n; ++k)
-            if (cl[k] < 0 || cl[k] >= M.nf) return ctx->fail(FETDPIC_EINVAL, "cell index out of range");
     }
+    // caller-supplied triangles are range-checked by the ingest kernel (reported at the next sync)
     // staging: x [n][2], u [n][2] (FP64), cell [n]
     const size_t bx = sizeof(double) * 2 * D.n, bc = sizeof(int) * D.n;
     char *st = (char *)xfer_buf(ctx, 2 * bx + bc);
@@ -997,9 +998,9 @@ extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const doub
     CK(cudaMemcpyAsync(st, x, bx, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(st + bx, u, bx, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(st + 2 * bx, cl, bc, cudaMemcpyHostToDevice, ctx->stream));
-    launch_ingest(ctx->stream, D.n, D.off, D.cell_off, ctx->p.precision == FETDPIC_FP32,
+    launch_ingest(ctx->stream, D.n, D.off, D.cell_off, M.nf, ctx->p.precision == FETDPIC_FP32,
                   (const double *)st, (const double *)(st + bx), (const int *)(st + 2 * bx), ctx->geo64,
-                  1.0 / ctx->p.c, ctx->cell, ctx->id, ctx->f[0], ctx->f[1], ctx->f[2], ctx->f[3]);
+                  1.0 / ctx->p.c, ctx->cell, ctx->id, ctx->f[0], ctx->f[1], ctx->f[2], ctx->f[3], ctx->status);
     CK(cudaGetLastError());
     if (!cell) CK(cudaStreamSynchronize(ctx->stream));   // `located` goes out of scope
     ctx->q_prev_valid = false;

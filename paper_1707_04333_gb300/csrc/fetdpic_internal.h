@@ -122,7 +122,8 @@ struct Species {
 };
 
 enum StatusBits : unsigned {
-    ST_WALK = 1u, ST_NONFINITE = 2u, ST_MESH = 4u, ST_TIMEOUT = 8u
+    ST_WALK = 1u, ST_NONFINITE = 2u, ST_MESH = 4u, ST_TIMEOUT = 8u,
+    ST_BADCELL = 16u                        // a written particle named a triangle outside its mesh
 };
 
 // ----------------------------------------------------------- launchers
@@ -227,9 +228,9 @@ size_t scan_tmp_ints(long long n);
 void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n, int *tmp);
 
 // Host-layout particle state into a species range (FP32: barycentrics, u/c).
-void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, bool fp32, const double *x,
+void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, int nf, bool fp32, const double *x,
                    const double *u, const int *cell, const Geo64 *geo, double inv_c, int *cell_o, int *id_o,
-                   void *f0, void *f1, void *f2, void *f3);
+                   void *f0, void *f1, void *f2, void *f3, unsigned *status);
 
 // Particle state to load order (FP32 converts barycentrics to coordinates).
 void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,

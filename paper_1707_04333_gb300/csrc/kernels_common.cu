@@ -255,15 +255,24 @@ void launch_sort(cudaStream_t st, const SortArgs &a)
 // Host-layout particle state (x, u in FP64, instance-local cell) into the
 // storage range of one species, in load order.  FP32 storage gets the
 // barycentric coordinates of x in its triangle and u/c.
-__global__ void k_ingest(long long n, long long off, int cell_off, int fp32, const double *__restrict__ x,
+// An instance-local triangle outside [0, nf) is never used as an address: the
+// particle becomes padding and ST_BADCELL reports it at the next sync.
+__global__ void k_ingest(long long n, long long off, int cell_off, int nf, int fp32, const double *__restrict__ x,
                          const double *__restrict__ u, const int *__restrict__ cell, const Geo64 *__restrict__ geo,
                          double inv_c, int *__restrict__ cell_o, int *__restrict__ id_o, void *f0, void *f1,
-                         void *f2, void *f3)
+                         void *f2, void *f3, unsigned *status)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const long long p = off + k;
-    const int c = cell_off + cell[k];
+    const int cl = cell[k];
+    if (cl < 0 || cl >= nf) {
+        cell_o[p] = -1;
+        id_o[p] = (int)k;
+        atomicOr(status, (unsigned)ST_BADCELL);
+        return;
+    }
+    const int c = cell_off + cl;
     cell_o[p] = c;
     id_o[p] = (int)k;
     const double px = x[2 * k], py = x[2 * k + 1];
@@ -283,13 +292,13 @@ __global__ void k_ingest(long long n, long long off, int cell_off, int fp32, con
     }
 }
 
-void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, bool fp32, const double *x,
+void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, int nf, bool fp32, const double *x,
                    const double *u, const int *cell, const Geo64 *geo, double inv_c, int *cell_o, int *id_o,
-                   void *f0, void *f1, void *f2, void *f3)
+                   void *f0, void *f1, void *f2, void *f3, unsigned *status)
 {
     if (n <= 0) return;
-    k_ingest<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, cell_off, fp32 ? 1 : 0, x, u, cell, geo, inv_c,
-                                                          cell_o, id_o, f0, f1, f2, f3);
+    k_ingest<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, cell_off, nf, fp32 ? 1 : 0, x, u, cell, geo,
+                                                          inv_c, cell_o, id_o, f0, f1, f2, f3, status);
 }
 
 __global__ void k_unsort64(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,

@@ -364,6 +364,18 @@ def test_edge_cases(fx):
         fetdpic.fetdpic_sync(sim.h)
     assert ei.value.code == fetdpic.EWALK
     sim.close()
+    # a triangle outside the mesh given to write_particles: found on the device, the particle dropped,
+    # EINVAL at the next sync
+    for prec in ("fp64", "fp32"):
+        sim = fetdpic.Simulation(w, precision=prec).load()
+        g = sim.read_species(0)
+        cells = g["cell"].copy()
+        cells[1] = len(m.triangles) + 5
+        fetdpic.fetdpic_write_particles(sim.h, 0, g["x"], g["u"], cells)
+        with pytest.raises(fetdpic.FetdpicError) as ei:
+            fetdpic.fetdpic_sync(sim.h)
+        assert ei.value.code == fetdpic.EINVAL and "outside the mesh" in str(ei.value)
+        sim.close()
     # a point outside the mesh is rejected at load
     bad = fetdpic.Simulation(inputs.Workload("o", m, [], 1e-10), precision="fp64")
     with pytest.raises(fetdpic.FetdpicError) as ei:
