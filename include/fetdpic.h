@@ -302,8 +302,9 @@ int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_ed
  * interval in {8, 16, 32}) combination -- only the sort interval for FP64,
  * nothing if sorting is off -- starting each from the current state, keeps
  * the fastest per step (sort cost included), and restores the particle and
- * field state exactly, so the simulation is unchanged.  trial_steps <= 0 =
- * 32.  The chosen values are returned in *variant and *sort_interval (each
+ * field state exactly, so the simulation is unchanged: the trials record no
+ * probe rows and run no checks, and a device error not yet reported by
+ * fetdpic_sync stays pending.  trial_steps <= 0 = 32.  The chosen values are returned in *variant and *sort_interval (each
  * may be NULL) and applied.  Blocks the calling thread. */
 int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, int *variant, int *sort_interval);
 

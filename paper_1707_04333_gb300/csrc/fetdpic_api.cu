@@ -1375,8 +1375,12 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     const bool keep_timed = ctx->p.time_stages != 0;
     const int keep_check = ctx->p.check_interval;
     const long long keep_steps = ctx->steps_done;
+    const long long keep_probes = ctx->probe_n;        // trial steps record no probe rows
+    unsigned keep_status = 0;                          // errors the caller has not read yet survive
+    CK(cudaMemcpy(&keep_status, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     ctx->p.time_stages = 0;
     ctx->p.check_interval = 0;
+    ctx->probe_n = 0;
     rc = copy_state(true);
     std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7} : std::vector<int>{3};
     std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 16, 32};
@@ -1408,8 +1412,9 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     // back to the saved state; the trials' currents are discarded
     if (!rc) rc = copy_state(false);
     CK(cudaMemsetAsync(ctx->ifix, 0, sizeof(unsigned long long) * ctx->E, ctx->stream));
-    CK(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaMemcpyAsync(ctx->status, &keep_status, sizeof(unsigned), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->probe_n = keep_probes;
     for (size_t k = 0; k < ctx->allocs.size(); ++k)
         if (ctx->allocs[k] == save) { ctx->allocs.erase(ctx->allocs.begin() + k); break; }
     if (ctx->p.dev_free) ctx->p.dev_free(save, ctx->p.alloc_user);

@@ -99,6 +99,27 @@ def test_probes_fp32_close_to_oracle(fx):
     sim.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotune_leaves_the_probe_record_alone(fx, precision):
+    """Autotuning between steps records no rows from its trial steps: the record equals that of the
+    same steps without tuning (the tuned kernel variant and sort interval give identical results)."""
+    fetdpic, _ = fx
+    w = _workload(55)
+    pts = _points(w, 20, 5)
+    out = []
+    for tune in (True, False):
+        s = fetdpic.Simulation(w, precision=precision, spai_level=1).load()
+        s.set_probes(pts, capacity=32)
+        s.step(3, "vay")
+        if tune:
+            s.autotune("vay", trial_steps=8)
+        s.step(5, "vay").sync()
+        out.append(s.read_probes())
+        s.close()
+    assert out[0][1] == out[1][1] == 8
+    assert np.array_equal(out[0][0], out[1][0])
+
+
 def test_probe_outside_mesh_rejected(fx):
     fetdpic, _ = fx
     w = _workload(54)
