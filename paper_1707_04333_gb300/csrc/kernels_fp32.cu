@@ -91,7 +91,35 @@ template <typename T> __device__ __forceinline__ T rcp_(T x);
 template <> __device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double rcp_<double>(double x) { return 1.0 / x; }
 
-template <int PUSHER, typename T>
+// FP64 1/sqrt(x) and 1/x for x in the FP32 normal range: a single-precision
+// seed refined by one Newton-Raphson step, y <- y (3 - x y^2) / 2 and
+// y <- y (2 - x y).  The relative error squares: at most about 1e-13 for the
+// square root (seed within 2.4e-7) and 4e-15 for the reciprocal, against
+// IEEE rounding, with a few FP64 operations instead of full-precision
+// square-root and division sequences.  Used by the high-gamma push of the FP32
+// path, whose results are stored in FP32.
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    const double y = (double)rsqrtf((float)x);
+    return y * (1.5 - 0.5 * x * (y * y));
+}
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    const double y = (double)__frcp_rn((float)x);
+    return y * (2.0 - x * y);
+}
+template <typename T, bool NEWTON> __device__ __forceinline__ T rsq(T x)
+{
+    if constexpr (NEWTON) return rsqrt_nr(x);
+    else return rsqrt_<T>(x);
+}
+template <typename T, bool NEWTON> __device__ __forceinline__ T rcq(T x)
+{
+    if constexpr (NEWTON) return rcp_nr(x);
+    else return rcp_<T>(x);
+}
+
+template <int PUSHER, typename T, bool NEWTON = false>
 __device__ __forceinline__ T push_c1(T &ux, T &uy, T ex, T ey, T bz)
 {
     const T one = T(1), half = T(0.5), two = T(2), four = T(4);
@@ -99,16 +127,16 @@ __device__ __forceinline__ T push_c1(T &ux, T &uy, T ex, T ey, T bz)
     if (PUSHER == FETDPIC_VAY) {
         // Sec. II.C(b): u' = u + 2 eps + v x beta; gamma^{n+1/2} from the quartic root
         // sqrt((sigma + sqrt(sigma^2 + 4|beta|^2))/2); t = beta/gamma; s = 1/(1+t^2)
-        const T ig0 = rsqrt_(one + ux * ux + uy * uy);
+        const T ig0 = rsq<T, NEWTON>(one + ux * ux + uy * uy);
         const T vx = ux * ig0, vy = uy * ig0;
         const T upx = ux + two * ex + vy * bz;
         const T upy = uy + two * ey - vx * bz;
         const T sigma = one + upx * upx + upy * upy - bb;
         const T r2 = sigma * sigma + four * bb;            // > 0: sigma >= 1 - |beta|^2 + |u'|^2 ...
-        const T root = r2 * rsqrt_(r2);
-        const T ign = rsqrt_(half * (sigma + root));        // 1/gamma^{n+1/2}
+        const T root = r2 * rsq<T, NEWTON>(r2);
+        const T ign = rsq<T, NEWTON>(half * (sigma + root));        // 1/gamma^{n+1/2}
         const T tz = bz * ign;
-        const T s = rcp_(one + tz * tz);
+        const T s = rcq<T, NEWTON>(one + tz * tz);
         ux = s * (upx + upy * tz);
         uy = s * (upy - upx * tz);
         return ign;
@@ -121,20 +149,20 @@ __device__ __forceinline__ T push_c1(T &ux, T &uy, T ex, T ey, T bz)
         // Sec. II.C(c): t = beta / gamma_H, gamma_H^2 = (sigma + sqrt(sigma^2 + 4|beta|^2))/2
         const T sigma = g2 - bb;
         const T r2 = sigma * sigma + four * bb;
-        const T root = r2 * rsqrt_(r2);
-        tz = bz * rsqrt_(half * (sigma + root));
+        const T root = r2 * rsq<T, NEWTON>(r2);
+        tz = bz * rsq<T, NEWTON>(half * (sigma + root));
     } else if (PUSHER == FETDPIC_BORIS_TAN) {
-        const T igbar = rsqrt_(g2);
+        const T igbar = rsq<T, NEWTON>(g2);
         const T nb = abs(bz);
         tz = (nb == T(0)) ? T(0) : (bz / nb) * tan(nb * igbar);
     } else {
-        tz = bz * rsqrt_(g2);
+        tz = bz * rsq<T, NEWTON>(g2);
     }
-    const T sz = (two * tz) * rcp_(one + tz * tz);
+    const T sz = (two * tz) * rcq<T, NEWTON>(one + tz * tz);
     const T uprx = umx + umy * tz, upry = umy - umx * tz;
     ux = (umx + upry * sz) + ex;
     uy = (umy - uprx * sz) + ey;
-    return rsqrt_(one + ux * ux + uy * uy);
+    return rsq<T, NEWTON>(one + ux * ux + uy * uy);
 }
 
 // FP64 push for gamma > 10 (rare; kept out of line so its registers do not
@@ -147,7 +175,7 @@ template <int PUSHER>
 __device__ __noinline__ PushOut push_fp64(float ux, float uy, float ex, float ey, float bz)
 {
     double dux = ux, duy = uy;
-    const double dig = push_c1<PUSHER, double>(dux, duy, (double)ex, (double)ey, (double)bz);
+    const double dig = push_c1<PUSHER, double, true>(dux, duy, (double)ex, (double)ey, (double)bz);
     PushOut o;
     o.ux = (float)dux; o.uy = (float)duy;
     o.vx = (float)(dux * dig); o.vy = (float)(duy * dig);
