@@ -161,6 +161,9 @@ BERNSTEIN_CASES = {
     # PEC square, 8,192 triangles, 327,680 particles, kT = 0.1 mc^2, omega_c/omega_p = 0.5
     "square": (lambda: inputs.pair_plasma(64, 20, kT=0.1, wc_over_wp=0.5, seed=2, pusher="vay"),
                128, 16384, (1, 2, 3, 4)),
+    # the benchmark workload itself: 200,978 triangles, 8,039,120 particles (16,384 steps of each path)
+    "pair-200k": (lambda: inputs.pair_plasma(317, 20, kT=0.1, wc_over_wp=0.5, seed=2, pusher="vay"),
+                  256, 16384, (1, 2, 3, 4)),
     # the paper's geometry (Sec. III.C): a 1024 x 4 strip periodic top and bottom (PEC in place of
     # PML at the ends), 8,192 triangles, 327,680 particles, kT = 0.05 mc^2, omega_p = 3 omega_c
     "periodic-strip": (lambda: inputs.pair_plasma(1024, 20, kT=0.05, wc_over_wp=1 / 3, seed=6, pusher="vay",
