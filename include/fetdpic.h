@@ -104,7 +104,7 @@ typedef struct {
     int kernel_variant;      /* FP32 particle kernel: 2, 3 or 4 = 256-thread blocks, that many
                                 resident per SM; 5 = particle state staged in shared memory by bulk
                                 asynchronous copies; 6 = 128-thread blocks, 7 per SM; 7 = 64-thread
-                                blocks, 14 per SM; 0 = default (3).  All give identical results. */
+                                blocks, 14 per SM; 0 = default (4).  All give identical results. */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);

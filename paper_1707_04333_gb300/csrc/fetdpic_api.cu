@@ -210,6 +210,9 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.block_size < 32 || P.block_size > 256 || (P.block_size & 31) || (SPECIES_ALIGN % P.block_size))
         return FETDPIC_EINVAL;
     if (P.record_walk < 0) return FETDPIC_EINVAL;
+    // untuned FP32 default: the register-prefetching kernel at 4 resident 256-thread blocks per SM
+    // (32 warps, 64 registers), measured fastest on the benchmark workload
+    if (P.kernel_variant == 0) P.kernel_variant = 4;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
     if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
@@ -1333,7 +1336,7 @@ extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interv
     if (!ctx) return FETDPIC_EINVAL;
     if (variant < 0 || variant > 7 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->p.kernel_variant = variant;
+    ctx->p.kernel_variant = variant == 0 ? 4 : variant;     // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
     drop_graphs(ctx);
     return FETDPIC_OK;
