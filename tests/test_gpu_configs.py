@@ -1,4 +1,4 @@
-"""GPU runs of the survey's workload shapes against closed forms and the oracle:
+"""GPU runs of the paper-shaped workloads against closed forms and the oracle:
 the relativistic cyclotron (10^4 steps, discrete orbit in closed form), its
 precision form (FP32 error budget), the high-gamma beam in crossed fields
 (FP64 push branch of the FP32 path), and a batch of uneven pair plasmas in one
@@ -85,7 +85,7 @@ def test_cyclotron_walk_stress_matches_oracle(fx):
 
 def test_cyclotron_precision_form_fp32(fx):
     """Precision form of the cyclotron case: FP32 path vs the FP64 oracle over 10^4 steps;
-    gyro-frequency error < 1e-4 (spec budget), |u| drift < 1e-4 (FP32 rounding of a rotation
+    gyro-frequency error < 1e-4 (the FP32 error budget), |u| drift < 1e-4 (FP32 rounding of a rotation
     that conserves |u| exactly in exact arithmetic), continuity residual at FP32 round-off every
     100 steps.  The FP32 residual is the rounding of the stored barycentrics (sum 1 to one FP32 ulp)
     relative to one step's barycentric displacement, here ~2.5e-3 (sub-cell orbits): ~ eps32 / 2.5e-3
