@@ -45,3 +45,22 @@ def test_invalid_arguments_rejected_without_gpu(libmod):
     assert L.fetdpic_set_external_profile(None, 0, None) == libmod.EINVAL
     assert L.fetdpic_set_external_amplitude(None, 0, 1.0) == libmod.EINVAL
     assert L.fetdpic_last_error(None) == b"null context"
+
+
+def test_header_is_plain_c99(libmod):
+    """A C program that uses only include/fetdpic.h compiles as strict C99 and links against the
+    library (no C++ or CUDA types at the boundary); it runs in tests/test_gpu_c_abi.py."""
+    import os
+    import subprocess
+    import tempfile
+    from paper_1707_04333_gb300 import build_lib
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(build_lib.LIB)
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "c_abi_roundtrip")
+        r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                            "-I", os.path.join(root, "include"), os.path.join(root, "tests", "c_abi_roundtrip.c"),
+                            "-L", libdir, "-lfetdpic", f"-Wl,-rpath,{libdir}", "-o", exe],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        assert os.path.exists(exe)
