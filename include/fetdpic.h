@@ -101,10 +101,12 @@ typedef struct {
     int block_size;          /* particle-kernel threads per block; 0 = tuned default */
     int use_graphs;          /* 1 = replay steps from a captured CUDA graph; 0 = plain launches */
     int time_stages;         /* 1 = record CUDA events between stages (fetdpic_stage_times) */
-    int kernel_variant;      /* FP32 particle kernel: 2, 3 or 4 = 256-thread blocks, that many
-                                resident per SM; 5 = particle state staged in shared memory by bulk
-                                asynchronous copies; 6 = 128-thread blocks, 7 per SM; 7 = 64-thread
-                                blocks, 14 per SM; 0 = default (4).  All give identical results. */
+    int kernel_variant;      /* FP32 particle kernel, one particle per thread: 2, 3 or 4 =
+                                256-thread blocks, that many resident per SM; 5 = particle state
+                                staged in shared memory by bulk asynchronous copies; 6 = 128-thread
+                                blocks, 7 per SM; 7 = 64-thread blocks, 14 per SM.  Two adjacent
+                                particles per thread: 8 = 256-thread blocks, 9 = 128, 10 = 64.
+                                0 = default (9).  All give identical results. */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);
@@ -298,7 +300,7 @@ int fetdpic_read_edges(fetdpic_ctx *ctx, int inst, int *edges);
 int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_edge, int *col, double *val);
 
 /* Autotuner (no counterpart in the paper, which reports no kernels): times
- * short trials of every (FP32 particle-kernel variant in {2, ..., 7}) x (sort
+ * short trials of every (FP32 particle-kernel variant in {2, ..., 10}) x (sort
  * interval in {8, 16, 32}) combination -- only the sort interval for FP64,
  * nothing if sorting is off -- starting each from the current state, keeps
  * the fastest per step (sort cost included), and restores the particle and
@@ -308,7 +310,7 @@ int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_ed
  * may be NULL) and applied.  Blocks the calling thread. */
 int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, int *variant, int *sort_interval);
 
-/* Apply a tuning found earlier (e.g. from a cache): variant 0 or 2-7;
+/* Apply a tuning found earlier (e.g. from a cache): variant 0 or 2-10;
  * sort_interval > 0, or < 0 for never. */
 int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval);
 

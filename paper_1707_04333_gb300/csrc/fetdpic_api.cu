@@ -21,7 +21,9 @@ constexpr double CODATA_EPS0 = 8.8541878128e-12;
 constexpr double CODATA_MU0 = 1.25663706212e-6;
 constexpr double CODATA_C = 299792458.0;
 constexpr long long SPECIES_ALIGN = 1024;   // species storage ranges start on this multiple
-constexpr int FP32_SHIFT = 25;              // fixed-point fraction bits of the FP32-path current
+// FP32-path current quantum 1/(2^25 - 64) of q_ref/dt: a per-particle contribution is at
+// most 2^25 - 60 in magnitude, so a warp's 64-particle run sum stays below 2^31.
+constexpr double FP32_SCALE = 33554368.0;
 
 struct StagedSpecies {
     int inst;
@@ -56,8 +58,8 @@ struct fetdpic_ctx {
     long long *m_soff = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
     float *m_v32 = nullptr, *r32 = nullptr;
     unsigned *status = nullptr;
-    std::vector<double> unit_host;           // per instance (q_ref/dt) 2^-shift
-    std::vector<int> shift;                  // per instance
+    std::vector<double> unit_host;           // per instance (q_ref/dt) / scale
+    std::vector<double> fixscale;            // per instance fixed-point scale (2^shift in FP64)
 
     // particles
     std::vector<StagedSpecies> staged;
@@ -210,9 +212,9 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.block_size < 32 || P.block_size > 256 || (P.block_size & 31) || (SPECIES_ALIGN % P.block_size))
         return FETDPIC_EINVAL;
     if (P.record_walk < 0) return FETDPIC_EINVAL;
-    // untuned FP32 default: the register-prefetching kernel at 4 resident 256-thread blocks per SM
-    // (32 warps, 64 registers), measured fastest on the benchmark workload
-    if (P.kernel_variant == 0) P.kernel_variant = 4;
+    // untuned FP32 default: two particles per thread in 128-thread blocks (20 warps per SM at
+    // 94 registers), measured fastest on the benchmark workload
+    if (P.kernel_variant == 0) P.kernel_variant = 9;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
     if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
@@ -505,7 +507,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     CK(cudaMemsetAsync(ctx->r, 0, sizeof(double) * ctx->E, ctx->stream));
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
     ctx->unit_host.assign(n_inst, 0.0);
-    ctx->shift.assign(n_inst, 0);
+    ctx->fixscale.assign(n_inst, 1.0);
     CK(cudaStreamSynchronize(ctx->stream));
     *out = holder.release();
     return FETDPIC_OK;
@@ -593,12 +595,10 @@ static int finalize(fetdpic_ctx *ctx)
         for (double w : wcell[k]) wmax = std::max(wmax, w);
         int sh = 62 - (int)std::ceil(std::log2(16.0 * wmax + 1.0));
         sh = std::max(20, std::min(52, sh));
-        // FP32 path: per-particle contributions are reduced across a warp in 32-bit
-        // integers, |contribution| <= 2^25 keeps a 32-lane sum below 2^31
-        if (P.precision == FETDPIC_FP32) sh = FP32_SHIFT;
-        ctx->shift[k] = sh;
+        // FP32 path: per-particle contributions are summed across a warp in 32-bit integers
+        ctx->fixscale[k] = P.precision == FETDPIC_FP32 ? FP32_SCALE : std::ldexp(1.0, sh);
         const double qr = qref[k] > 0 ? qref[k] : 1.0;
-        ctx->unit_host[k] = (qr / ctx->inst[k].dt) * std::ldexp(1.0, -sh);
+        ctx->unit_host[k] = (qr / ctx->inst[k].dt) / ctx->fixscale[k];
     }
     ctx->sp.resize(ns);
     long long off = 0, packed = 0, hist_n = 0;
@@ -612,7 +612,7 @@ static int finalize(fetdpic_ctx *ctx)
         const double dt = I.dt;
         D.alpha = S.q * dt / (2.0 * S.m);
         const double qr = qref[S.inst] > 0 ? qref[S.inst] : 1.0;
-        D.wfix = (S.q / qr) * std::ldexp(1.0, ctx->shift[S.inst]);
+        D.wfix = (S.q / qr) * ctx->fixscale[S.inst];
         D.qfix = D.wfix;
         D.wfix32 = (float)D.wfix;
         D.dt = dt; D.c = P.c; D.ic2 = 1.0 / (P.c * P.c);
@@ -717,7 +717,7 @@ static int finalize(fetdpic_ctx *ctx)
     rc = rc ? rc : upload(ctx, ctx->inst_unit, ctx->unit_host.data(), ctx->unit_host.size());
     if (ctx->qunit) {
         std::vector<double> qu(ni);
-        for (int k = 0; k < ni; ++k) qu[k] = (qref[k] > 0 ? qref[k] : 1.0) * std::ldexp(1.0, -ctx->shift[k]);
+        for (int k = 0; k < ni; ++k) qu[k] = (qref[k] > 0 ? qref[k] : 1.0) / ctx->fixscale[k];
         rc = rc ? rc : upload(ctx, ctx->qunit, qu.data(), qu.size());
     }
     if (rc) return rc;
@@ -1334,9 +1334,9 @@ static void drop_graphs(fetdpic_ctx *ctx)
 extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)
 {
     if (!ctx) return FETDPIC_EINVAL;
-    if (variant < 0 || variant > 7 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
+    if (variant < 0 || variant > 10 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->p.kernel_variant = variant == 0 ? 4 : variant;     // 0 = the untuned default
+    ctx->p.kernel_variant = variant == 0 ? 9 : variant;     // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
     drop_graphs(ctx);
     return FETDPIC_OK;
@@ -1385,7 +1385,7 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     ctx->p.check_interval = 0;
     ctx->probe_n = 0;
     rc = copy_state(true);
-    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7} : std::vector<int>{3};
+    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10} : std::vector<int>{3};
     std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 16, 32};
     double best = 1e300;
     int bv = keep_variant, bs = keep_sort;

@@ -86,7 +86,7 @@ static_assert(sizeof(Cst32) == 48, "Cst32 layout");
 struct __align__(16) Sp32 {
     float kappa;                            // q/m
     float xe_x, xe_y, xb;                   // external fields pre-scaled (alpha E/c, alpha B)
-    float wfix;                             // (q / q_ref) * 2^shift32
+    float wfix;                             // (q / q_ref) * (2^25 - 64)
     int inst, edge_off, pad;
 };
 

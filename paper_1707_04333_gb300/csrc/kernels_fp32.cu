@@ -184,8 +184,9 @@ __device__ __noinline__ PushOut push_fp64(float ux, float uy, float ex, float ey
 }
 
 // Fixed-point current of one sub-segment, Eq. (I.assign): round(w (l_a^s l_b^f
-// - l_a^f l_b^s)) per local edge m = (a, b) = (m+1, m+2); |.| <= 2^shift32, so a
-// sum over one warp fits in 32 bits.
+// - l_a^f l_b^s)) per local edge m = (a, b) = (m+1, m+2); |w| <= 2^25 - 64 and
+// |l_a^s l_b^f - l_a^f l_b^s| <= 1 (to FP32 rounding), so a sum over 64 particles
+// fits in 32 bits.
 __device__ __forceinline__ void seg_current32(const float *ls, const float *lf, float w, int *v)
 {
 #pragma unroll
@@ -491,6 +492,178 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32(StepArgs32 a)
     drain(a, q, qhead, qtail, lane);
 }
 
+// ------------------------------------------------- two particles per lane
+// Each lane takes two adjacent particles, so a warp chunk is 64 particles and
+// the state moves in 8-byte vector loads and stores.  When both particles of
+// a lane stay in the same triangle their currents are summed in the lane, so
+// the warp-segmented reduction runs once per 64 particles; a lane whose pair
+// straddles a change of triangle deposits its first particle with its own
+// integer atomics.  The per-particle arithmetic is process_chunk's, written out
+// the same way.
+constexpr int P32_QUEUE2 = 128;              // walker ring per warp: 31 pending + 64 new fit
+
+struct PState2 { int fa, fb, sp; float2 l0, l1, ux, uy; };
+
+__device__ __forceinline__ PState2 load_state2(const StepArgs32 &a, unsigned c, int lane)
+{
+    const unsigned p = c * 64u + 2u * (unsigned)lane;
+    PState2 s;
+    const int2 f = __ldcs(reinterpret_cast<const int2 *>(a.cell + p));
+    s.fa = f.x; s.fb = f.y;
+    s.l0 = __ldcs(reinterpret_cast<const float2 *>(a.l0 + p));
+    s.l1 = __ldcs(reinterpret_cast<const float2 *>(a.l1 + p));
+    s.ux = __ldcs(reinterpret_cast<const float2 *>(a.ux + p));
+    s.uy = __ldcs(reinterpret_cast<const float2 *>(a.uy + p));
+    s.sp = __ldg(a.chunk_sp + 2 * c);
+    return s;
+}
+
+// Result of one particle's gather, push and in-triangle test.
+struct POne {
+    float ux, uy, vx, vy, lf0, lf1;
+    int key;                                 // triangle if it stays, else -1
+    bool walking;
+    int v[3];                                // fixed-point current if it stays, else 0
+};
+
+template <int PUSHER>
+__device__ __forceinline__ POne one_particle(const StepArgs32 &a, const float4 &s0, float wfix, int f,
+                                             float l0, float l1, float ux, float uy, const PRec &r)
+{
+    POne o;
+    const bool live = f >= 0;
+    const float l2 = 1.f - l0 - l1;
+    const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
+    const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
+    const float bz = s0.x * r.r1.z + s0.w;
+    float ig, vx, vy;
+    if (1.f + ux * ux + uy * uy > 100.f) {
+        const PushOut q = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
+        ux = q.ux; uy = q.uy; vx = q.vx; vy = q.vy; ig = q.ig;
+    } else {
+        ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
+        vx = ux * ig; vy = uy * ig;
+    }
+    if (live && !isfinite(vx + vy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    const float g0 = r.c0.x * vx + r.c0.y * vy;
+    const float g1 = r.c0.z * vx + r.c0.w * vy;
+    const float g2 = r.c1.x * vx + r.c1.y * vy;
+    const float lf0 = l0 + g0, lf1 = l1 + g1;
+    const bool stays = lf0 >= 0.f && lf1 >= 0.f && l2 + g2 >= 0.f;
+    const float wk = (live && stays) ? wfix : 0.f;
+    o.v[0] = __float2int_rn((l1 * g2 - g1 * l2) * wk);
+    o.v[1] = __float2int_rn((l2 * g0 - g2 * l0) * wk);
+    o.v[2] = __float2int_rn((l0 * g1 - g0 * l1) * wk);
+    o.ux = ux; o.uy = uy; o.vx = vx; o.vy = vy; o.lf0 = lf0; o.lf1 = lf1;
+    o.key = (live && stays) ? f : -1;
+    o.walking = live && !stays;
+    return o;
+}
+
+__device__ __forceinline__ WalkItem walk_item(long long p, int f, int sp, float l0, float l1, const POne &o)
+{
+    WalkItem it;
+    it.p = p; it.f = f; it.sp = sp;
+    it.l0 = l0; it.l1 = l1; it.l2 = 1.f - l0 - l1; it.pad = 0.f;
+    it.ux = o.ux; it.uy = o.uy; it.vx = o.vx; it.vy = o.vy;
+    return it;
+}
+
+template <int PUSHER>
+__device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, int lane, const PState2 &s,
+                                               const PRec &ra, const PRec &rb, WalkItem *q, unsigned &qhead,
+                                               unsigned &qtail)
+{
+    const unsigned full = 0xffffffffu;
+    const unsigned pa = c * 64u + 2u * (unsigned)lane;
+    const Sp32 *spp = a.sp + s.sp;
+    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
+    const float wfix = __ldg(&spp->wfix);
+    const POne A = one_particle<PUSHER>(a, s0, wfix, s.fa, s.l0.x, s.l1.x, s.ux.x, s.uy.x, ra);
+    const POne B = one_particle<PUSHER>(a, s0, wfix, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
+    // walkers to the ring
+    const unsigned lt = (1u << lane) - 1u;
+    const unsigned wa = __ballot_sync(full, A.walking), wb = __ballot_sync(full, B.walking);
+    if (A.walking) q[(qtail + __popc(wa & lt)) & (P32_QUEUE2 - 1)] = walk_item(pa, s.fa, s.sp, s.l0.x, s.l1.x, A);
+    qtail += __popc(wa);
+    if (B.walking) q[(qtail + __popc(wb & lt)) & (P32_QUEUE2 - 1)] = walk_item(pa + 1, s.fb, s.sp, s.l0.y, s.l1.y, B);
+    qtail += __popc(wb);
+    // current of the particles that stay, Eq. (I.assign)
+    const bool same = A.key == B.key;
+    if (!same && A.key >= 0) {
+        const int ew[3] = {__float_as_int(ra.r1.w), __float_as_int(ra.c1.z), __float_as_int(ra.c1.w)};
+        add_seg32(a.ifix, ew, A.v);
+    }
+    int v0[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) v0[m] = B.v[m] + (same ? A.v[m] : 0);
+    const int key = B.key;
+    {
+        const int kn = __shfl_down_sync(full, key, 1);
+        const unsigned tails = __ballot_sync(full, (lane == 31) || (kn != key));
+        const int seg_end = lane + __ffs(tails >> lane) - 1;
+        const int kp = __shfl_up_sync(full, key, 1);
+        const bool head = (lane == 0) || (kp != key);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o0 = __shfl_down_sync(full, v0[0], off);
+            const int o1 = __shfl_down_sync(full, v0[1], off);
+            const int o2 = __shfl_down_sync(full, v0[2], off);
+            if (lane + off <= seg_end) { v0[0] += o0; v0[1] += o1; v0[2] += o2; }
+        }
+        if (head && key >= 0) {
+            const int ew[3] = {__float_as_int(rb.r1.w), __float_as_int(rb.c1.z), __float_as_int(rb.c1.w)};
+            add_seg32(a.ifix, ew, v0);
+        }
+    }
+    // state: both slots of every lane are written (a walker's slot is rewritten by its
+    // walk after the warp barrier below, a padding slot keeps its value)
+    const bool sa = A.key >= 0, sb = B.key >= 0;
+    __stcs(reinterpret_cast<float2 *>(a.l0 + pa), make_float2(sa ? A.lf0 : s.l0.x, sb ? B.lf0 : s.l0.y));
+    __stcs(reinterpret_cast<float2 *>(a.l1 + pa), make_float2(sa ? A.lf1 : s.l1.x, sb ? B.lf1 : s.l1.y));
+    __stcs(reinterpret_cast<float2 *>(a.ux + pa), make_float2(sa ? A.ux : s.ux.x, sb ? B.ux : s.ux.y));
+    __stcs(reinterpret_cast<float2 *>(a.uy + pa), make_float2(sa ? A.uy : s.uy.x, sb ? B.uy : s.uy.y));
+    if (a.rec_cap > 0) {
+        if (sa) a.rec_cnt[pa] = 0;
+        if (sb) a.rec_cnt[pa + 1] = 0;
+    }
+    while (qtail - qhead >= 32) {
+        __syncwarp();
+        const WalkItem w = q[(qhead + lane) & (P32_QUEUE2 - 1)];
+        walk_particle(a, w);
+        qhead += 32;
+        __syncwarp();
+    }
+}
+
+template <int PUSHER, int MINB, int NW>
+__global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
+{
+    __shared__ WalkItem qbuf[NW][P32_QUEUE2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WalkItem *q = qbuf[warp];
+    unsigned qhead = 0, qtail = 0;
+    const unsigned nwarps = gridDim.x * NW;
+    const unsigned wid = blockIdx.x * NW + warp;
+    const long long n64 = a.nchunks / 2;         // species ranges are padded to 1024, so nchunks is even
+    const unsigned K = (unsigned)((n64 + nwarps - 1) / nwarps);
+    unsigned c = wid * K;
+    const unsigned cend = (unsigned)min((long long)c + K, n64);
+    if (c >= cend) return;
+    PState2 sn = load_state2(a, c, lane);
+    for (; c < cend; ++c) {
+        const PState2 s = sn;
+        if (c + 1 < cend) sn = load_state2(a, c + 1, lane);
+        const PRec ra = load_rec(a, s.fa), rb = load_rec(a, s.fb);
+        process_chunk2<PUSHER>(a, c, lane, s, ra, rb, q, qhead, qtail);
+    }
+    const unsigned left = qtail - qhead;
+    if (left > 0) {
+        __syncwarp();
+        if ((unsigned)lane < left) walk_particle(a, q[(qhead + lane) & (P32_QUEUE2 - 1)]);
+    }
+}
+
 // ------------------------------------------------------- staged variant
 // Particle state streamed into shared memory by bulk asynchronous copies
 // (cp.async.bulk, completion on an mbarrier), ST_DEPTH chunks ahead of the
@@ -635,6 +808,24 @@ static void launch_p32(cudaStream_t st, const StepArgs32 &a)
     k_particles32<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
 }
 
+template <int PUSHER, int MINB, int NW>
+static void launch_p32x2(cudaStream_t st, const StepArgs32 &a)
+{
+    static int per_sm = 0, sms = 0, dev = -1;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev || per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32x2<PUSHER, MINB, NW>, NW * 32, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        dev = d;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long need = (a.nchunks / 2 + NW - 1) / NW;
+    const long long grid = std::min<long long>(need, (long long)per_sm * sms);
+    if (grid <= 0) return;
+    k_particles32x2<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
+}
+
 template <int PUSHER>
 static void launch_p32s(cudaStream_t st, const StepArgs32 &a)
 {
@@ -660,6 +851,9 @@ static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
     case 5: launch_p32s<PUSHER>(st, a); break;
     case 6: launch_p32<PUSHER, 7, 4>(st, a); break;
     case 7: launch_p32<PUSHER, 14, 2>(st, a); break;
+    case 8: launch_p32x2<PUSHER, 2, 8>(st, a); break;
+    case 9: launch_p32x2<PUSHER, 5, 4>(st, a); break;
+    case 10: launch_p32x2<PUSHER, 10, 2>(st, a); break;
     case 2: launch_p32<PUSHER, 2>(st, a); break;
     case 4: launch_p32<PUSHER, 4>(st, a); break;
     default: launch_p32<PUSHER, 3>(st, a); break;     // measured best on GB300 (no spills, 24 warps/SM)
