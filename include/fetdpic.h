@@ -105,8 +105,10 @@ typedef struct {
                                 256-thread blocks, that many resident per SM; 5 = particle state
                                 staged in shared memory by bulk asynchronous copies; 6 = 128-thread
                                 blocks, 7 per SM; 7 = 64-thread blocks, 14 per SM.  Two adjacent
-                                particles per thread: 8 = 256-thread blocks, 9 = 128, 10 = 64.
-                                0 = default (9).  All give identical results. */
+                                particles per thread: 8 = 256-thread blocks, 9 = 128, 10 = 64;
+                                11 = 128 and 12 = 64 with the two particles' triangle records read
+                                one after the other (fewer registers, 24 warps per SM).
+                                0 = default (11).  All give identical results. */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);
@@ -300,7 +302,7 @@ int fetdpic_read_edges(fetdpic_ctx *ctx, int inst, int *edges);
 int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_edge, int *col, double *val);
 
 /* Autotuner (no counterpart in the paper, which reports no kernels): times
- * short trials of every (FP32 particle-kernel variant in {2, ..., 10}) x (sort
+ * short trials of every (FP32 particle-kernel variant in {2, ..., 12}) x (sort
  * interval in {8, 16, 32}) combination -- only the sort interval for FP64,
  * nothing if sorting is off -- starting each from the current state, keeps
  * the fastest per step (sort cost included), and restores the particle and
@@ -310,7 +312,7 @@ int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_ed
  * may be NULL) and applied.  Blocks the calling thread. */
 int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, int *variant, int *sort_interval);
 
-/* Apply a tuning found earlier (e.g. from a cache): variant 0 or 2-10;
+/* Apply a tuning found earlier (e.g. from a cache): variant 0 or 2-12;
  * sort_interval > 0, or < 0 for never. */
 int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval);
 

@@ -212,9 +212,9 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.block_size < 32 || P.block_size > 256 || (P.block_size & 31) || (SPECIES_ALIGN % P.block_size))
         return FETDPIC_EINVAL;
     if (P.record_walk < 0) return FETDPIC_EINVAL;
-    // untuned FP32 default: two particles per thread in 128-thread blocks (20 warps per SM at
-    // 94 registers), measured fastest on the benchmark workload
-    if (P.kernel_variant == 0) P.kernel_variant = 9;
+    // untuned FP32 default: two particles per thread in 128-thread blocks, records read one
+    // particle at a time (24 warps per SM at 80 registers), measured fastest on the benchmark workload
+    if (P.kernel_variant == 0) P.kernel_variant = 11;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
     if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
@@ -1334,9 +1334,9 @@ static void drop_graphs(fetdpic_ctx *ctx)
 extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)
 {
     if (!ctx) return FETDPIC_EINVAL;
-    if (variant < 0 || variant > 10 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
+    if (variant < 0 || variant > 12 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->p.kernel_variant = variant == 0 ? 9 : variant;     // 0 = the untuned default
+    ctx->p.kernel_variant = variant == 0 ? 11 : variant;    // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
     drop_graphs(ctx);
     return FETDPIC_OK;
@@ -1385,7 +1385,7 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     ctx->p.check_interval = 0;
     ctx->probe_n = 0;
     rc = copy_state(true);
-    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10} : std::vector<int>{3};
+    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12} : std::vector<int>{3};
     std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 16, 32};
     double best = 1e300;
     int bv = keep_variant, bs = keep_sort;

@@ -569,9 +569,13 @@ __device__ __forceinline__ WalkItem walk_item(long long p, int f, int sp, float 
     return it;
 }
 
-template <int PUSHER>
+// SEQ: the second particle's records are loaded after the first particle's
+// arithmetic (a compiler barrier keeps them there), so the two record sets are
+// never live together; when both particles share a triangle the second load
+// hits L1.
+template <int PUSHER, bool SEQ>
 __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, int lane, const PState2 &s,
-                                               const PRec &ra, const PRec &rb, WalkItem *q, unsigned &qhead,
+                                               const PRec &ra, const PRec &rb_in, WalkItem *q, unsigned &qhead,
                                                unsigned &qtail)
 {
     const unsigned full = 0xffffffffu;
@@ -580,6 +584,13 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
     const float wfix = __ldg(&spp->wfix);
     const POne A = one_particle<PUSHER>(a, s0, wfix, s.fa, s.l0.x, s.l1.x, s.ux.x, s.uy.x, ra);
+    PRec rb;
+    if (SEQ) {
+        asm volatile("" ::: "memory");
+        rb = load_rec(a, s.fb);
+    } else {
+        rb = rb_in;
+    }
     const POne B = one_particle<PUSHER>(a, s0, wfix, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
     // walkers to the ring
     const unsigned lt = (1u << lane) - 1u;
@@ -636,7 +647,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     }
 }
 
-template <int PUSHER, int MINB, int NW>
+template <int PUSHER, int MINB, int NW, bool SEQ>
 __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
 {
     __shared__ WalkItem qbuf[NW][P32_QUEUE2];
@@ -654,8 +665,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
     for (; c < cend; ++c) {
         const PState2 s = sn;
         if (c + 1 < cend) sn = load_state2(a, c + 1, lane);
-        const PRec ra = load_rec(a, s.fa), rb = load_rec(a, s.fb);
-        process_chunk2<PUSHER>(a, c, lane, s, ra, rb, q, qhead, qtail);
+        const PRec ra = load_rec(a, s.fa);
+        PRec rb;
+        if (!SEQ) rb = load_rec(a, s.fb);
+        process_chunk2<PUSHER, SEQ>(a, c, lane, s, ra, rb, q, qhead, qtail);
     }
     const unsigned left = qtail - qhead;
     if (left > 0) {
@@ -808,14 +821,14 @@ static void launch_p32(cudaStream_t st, const StepArgs32 &a)
     k_particles32<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
 }
 
-template <int PUSHER, int MINB, int NW>
+template <int PUSHER, int MINB, int NW, bool SEQ = false>
 static void launch_p32x2(cudaStream_t st, const StepArgs32 &a)
 {
     static int per_sm = 0, sms = 0, dev = -1;
     int d = 0;
     cudaGetDevice(&d);
     if (d != dev || per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32x2<PUSHER, MINB, NW>, NW * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32x2<PUSHER, MINB, NW, SEQ>, NW * 32, 0);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         dev = d;
         if (per_sm < 1) per_sm = 1;
@@ -823,7 +836,7 @@ static void launch_p32x2(cudaStream_t st, const StepArgs32 &a)
     const long long need = (a.nchunks / 2 + NW - 1) / NW;
     const long long grid = std::min<long long>(need, (long long)per_sm * sms);
     if (grid <= 0) return;
-    k_particles32x2<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
+    k_particles32x2<PUSHER, MINB, NW, SEQ><<<(unsigned)grid, NW * 32, 0, st>>>(a);
 }
 
 template <int PUSHER>
@@ -854,6 +867,8 @@ static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
     case 8: launch_p32x2<PUSHER, 2, 8>(st, a); break;
     case 9: launch_p32x2<PUSHER, 5, 4>(st, a); break;
     case 10: launch_p32x2<PUSHER, 10, 2>(st, a); break;
+    case 11: launch_p32x2<PUSHER, 6, 4, true>(st, a); break;
+    case 12: launch_p32x2<PUSHER, 12, 2, true>(st, a); break;
     case 2: launch_p32<PUSHER, 2>(st, a); break;
     case 4: launch_p32<PUSHER, 4>(st, a); break;
     default: launch_p32<PUSHER, 3>(st, a); break;     // measured best on GB300 (no spills, 24 warps/SM)

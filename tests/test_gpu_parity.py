@@ -229,7 +229,7 @@ def test_fp32_kernel_variants_bit_identical(fx):
     fetdpic, _ = fx
     w = inputs.pair_plasma(48, 24, kT=0.3, seed=23, pusher="vay")
     outs = {}
-    for v in (3, 2, 4, 5, 6, 7, 8, 9, 10):
+    for v in (3, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12):
         s = fetdpic.Simulation(w, precision="fp32", spai_level=1, sort_interval=4, kernel_variant=v,
                                check_interval=5).load()
         s.step(5, "vay").step(4, "hc").step(6, "boris").sync()
@@ -237,7 +237,7 @@ def test_fp32_kernel_variants_bit_identical(fx):
         assert c["dce"] < 2e-5, (v, c)
         outs[v] = (s.read_fields(), s.read_species(0), s.read_species(1))
         s.close()
-    for v in (2, 4, 5, 6, 7, 8, 9, 10):
+    for v in (2, 4, 5, 6, 7, 8, 9, 10, 11, 12):
         for a, b in zip(outs[3], outs[v]):
             for k in a:
                 assert np.array_equal(a[k], b[k]), (v, k)
