@@ -197,12 +197,14 @@ __device__ __forceinline__ void seg_current32(const float *ls, const float *lf, 
     }
 }
 
+// Three integer atomics, issued whatever their value (adding 0 changes nothing,
+// and a test would cost a divergent branch per edge).
 __device__ __forceinline__ void add_seg32(unsigned long long *ifix, const int *ew, const int *v)
 {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         const long long s = (ew[m] & 1) ? -(long long)v[m] : (long long)v[m];
-        if (s != 0) atomicAdd(ifix + (ew[m] >> 1), (unsigned long long)s);
+        atomicAdd(ifix + (ew[m] >> 1), (unsigned long long)s);
     }
 }
 
@@ -522,7 +524,7 @@ __device__ __forceinline__ PState2 load_state2(const StepArgs32 &a, unsigned c, 
 struct POne {
     float ux, uy, vx, vy, lf0, lf1;
     int key;                                 // triangle if it stays, else -1
-    bool walking;
+    bool walking, bad;                       // bad: a live particle's velocity is not finite
     int v[3];                                // fixed-point current if it stays, else 0
 };
 
@@ -544,7 +546,7 @@ __device__ __forceinline__ POne one_particle(const StepArgs32 &a, const float4 &
         ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
         vx = ux * ig; vy = uy * ig;
     }
-    if (live && !isfinite(vx + vy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    o.bad = live && !isfinite(vx + vy);
     const float g0 = r.c0.x * vx + r.c0.y * vy;
     const float g1 = r.c0.z * vx + r.c0.w * vy;
     const float g2 = r.c1.x * vx + r.c1.y * vy;
@@ -576,7 +578,7 @@ __device__ __forceinline__ WalkItem walk_item(long long p, int f, int sp, float 
 template <int PUSHER, bool SEQ>
 __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, int lane, const PState2 &s,
                                                const PRec &ra, const PRec &rb_in, WalkItem *q, unsigned &qhead,
-                                               unsigned &qtail)
+                                               unsigned &qtail, bool &bad)
 {
     const unsigned full = 0xffffffffu;
     const unsigned pa = c * 64u + 2u * (unsigned)lane;
@@ -592,6 +594,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
         rb = rb_in;
     }
     const POne B = one_particle<PUSHER>(a, s0, wfix, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
+    bad |= A.bad | B.bad;
     // walkers to the ring
     const unsigned lt = (1u << lane) - 1u;
     const unsigned wa = __ballot_sync(full, A.walking), wb = __ballot_sync(full, B.walking);
@@ -661,6 +664,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
     unsigned c = wid * K;
     const unsigned cend = (unsigned)min((long long)c + K, n64);
     if (c >= cend) return;
+    bool bad = false;
     PState2 sn = load_state2(a, c, lane);
     for (; c < cend; ++c) {
         const PState2 s = sn;
@@ -668,8 +672,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
         const PRec ra = load_rec(a, s.fa);
         PRec rb;
         if (!SEQ) rb = load_rec(a, s.fb);
-        process_chunk2<PUSHER, SEQ>(a, c, lane, s, ra, rb, q, qhead, qtail);
+        process_chunk2<PUSHER, SEQ>(a, c, lane, s, ra, rb, q, qhead, qtail, bad);
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
     const unsigned left = qtail - qhead;
     if (left > 0) {
         __syncwarp();

@@ -376,6 +376,17 @@ def test_edge_cases(fx):
             fetdpic.fetdpic_sync(sim.h)
         assert ei.value.code == fetdpic.EINVAL and "outside the mesh" in str(ei.value)
         sim.close()
+    # an overflowing field makes the momenta non-finite: reported as ENONFINITE at the next sync
+    # (with NaN positions the walk finds no exit edge, so every triangle index stays valid)
+    for prec in ("fp64", "fp32"):
+        sim = fetdpic.Simulation(w, precision=prec).load()
+        ne = sim.read_fields()["e"].shape[0]
+        fetdpic.fetdpic_write_fields(sim.h, 0, e=np.full(ne, 1e300))
+        fetdpic.fetdpic_step(sim.h, 2, "vay")
+        with pytest.raises(fetdpic.FetdpicError) as ei:
+            fetdpic.fetdpic_sync(sim.h)
+        assert ei.value.code == fetdpic.ENONFINITE, (prec, ei.value)
+        sim.close()
     # a point outside the mesh is rejected at load
     bad = fetdpic.Simulation(inputs.Workload("o", m, [], 1e-10), precision="fp64")
     with pytest.raises(fetdpic.FetdpicError) as ei:
