@@ -89,6 +89,7 @@ struct __align__(16) Sp32 {
     float wfix;                             // (q / q_ref) * (2^25 - 64)
     int inst, edge_off, pad;
 };
+static_assert(sizeof(Sp32) == 32, "Sp32 layout");
 
 // Topology: edge word = (global edge << 1) | (sign < 0); neighbour word =
 // (global triangle << 2) | local index of the shared edge there, -1 on a wall.

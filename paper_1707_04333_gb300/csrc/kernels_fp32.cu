@@ -246,10 +246,18 @@ struct WalkItem {
 };
 static_assert(sizeof(WalkItem) == 48, "WalkItem layout");
 
+// 32 bytes (32-byte aligned) in one 256-bit load.
+__device__ __forceinline__ void ld_v8(const void *p, float4 &x, float4 &y)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(x.x), "=f"(x.y), "=f"(x.z), "=f"(x.w), "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+        : "l"(p));
+}
+
 __device__ __forceinline__ void load_cst(const Cst32 *cst, int f, float *G, int *ew, int *nb)
 {
     const float4 *cp = reinterpret_cast<const float4 *>(cst + f);
-    const float4 c0 = cp[0], c1 = cp[1], c2 = cp[2];
+    const float4 c0 = __ldg(cp), c1 = __ldg(cp + 1), c2 = __ldg(cp + 2);
     G[0] = c0.x; G[1] = c0.y; G[2] = c0.z; G[3] = c0.w; G[4] = c1.x; G[5] = c1.y;
     ew[0] = __float_as_int(c2.w); ew[1] = __float_as_int(c1.z); ew[2] = __float_as_int(c1.w);
     nb[0] = __float_as_int(c2.x); nb[1] = __float_as_int(c2.y); nb[2] = __float_as_int(c2.z);
@@ -259,7 +267,9 @@ __device__ __forceinline__ void load_cst(const Cst32 *cst, int f, float *G, int 
 // through the triangles it crosses (the current splits the path per triangle,
 // Eq. (I.assign)): exit test, deposit of each sub-segment with direct integer
 // atomics, hand-off to the neighbour or specular reflection at a PEC wall, and
-// the final particle state.
+// the final particle state.  U_STORED: the caller has already stored the pushed
+// momentum, so it is written again only when a wall reflected it.
+template <bool U_STORED = false>
 __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkItem it)
 {
     const Sp32 *spp = a.sp + it.sp;
@@ -269,6 +279,7 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
     int f = it.f, ncross = 0, min = -1;
     float lin[3] = {it.l0, it.l1, it.l2};
     float tin = 0.f, ux = it.ux, uy = it.uy, vx = it.vx, vy = it.vy;
+    bool reflected = false;
     float lfin[3];
     float G[6];
     int ew[3], nb[3];
@@ -316,6 +327,7 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
             const float pv = (vx * gxb + vy * gyb) * igg;
             vx -= 2.f * pv * gxb; vy -= 2.f * pv * gyb;
             min = best;
+            reflected = true;
         } else {
             // hand-off: the neighbour's node m2+1 is our node best+2, its m2+2 our best+1
             const int m2 = nbw & 3;
@@ -330,7 +342,7 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
         }
     }
     a.l0[p] = lfin[0]; a.l1[p] = lfin[1];
-    a.ux[p] = ux; a.uy[p] = uy;
+    if (!U_STORED || reflected) { a.ux[p] = ux; a.uy[p] = uy; }
     a.cell[p] = f;
     if (a.rec_cap > 0) a.rec_cnt[p] = ncross;
 }
@@ -361,7 +373,8 @@ __device__ __forceinline__ PRec load_rec(const StepArgs32 &a, int f)
     const float4 *cp = reinterpret_cast<const float4 *>(a.cst + g);
     const float4 *rp = reinterpret_cast<const float4 *>(a.rec + g);
     PRec r;
-    r.c0 = __ldg(cp); r.c1 = __ldg(cp + 1); r.r0 = __ldg(rp); r.r1 = __ldg(rp + 1);
+    r.c0 = __ldg(cp); r.c1 = __ldg(cp + 1);    // constants (48-byte stride: 16-byte loads)
+    ld_v8(rp, r.r0, r.r1);                     // field record, 32-byte aligned: one 256-bit load
     return r;
 }
 
@@ -630,13 +643,14 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
             add_seg32(a.ifix, ew, v0);
         }
     }
-    // state: both slots of every lane are written (a walker's slot is rewritten by its
-    // walk after the warp barrier below, a padding slot keeps its value)
-    const bool sa = A.key >= 0, sb = B.key >= 0;
+    // state: both slots of every lane are written (a walker's position is rewritten by its
+    // walk after the warp barrier below, and its momentum only if a wall reflects it; a
+    // padding slot keeps its value)
+    const bool sa = A.key >= 0, sb = B.key >= 0, la = s.fa >= 0, lb = s.fb >= 0;
     __stcs(reinterpret_cast<float2 *>(a.l0 + pa), make_float2(sa ? A.lf0 : s.l0.x, sb ? B.lf0 : s.l0.y));
     __stcs(reinterpret_cast<float2 *>(a.l1 + pa), make_float2(sa ? A.lf1 : s.l1.x, sb ? B.lf1 : s.l1.y));
-    __stcs(reinterpret_cast<float2 *>(a.ux + pa), make_float2(sa ? A.ux : s.ux.x, sb ? B.ux : s.ux.y));
-    __stcs(reinterpret_cast<float2 *>(a.uy + pa), make_float2(sa ? A.uy : s.uy.x, sb ? B.uy : s.uy.y));
+    __stcs(reinterpret_cast<float2 *>(a.ux + pa), make_float2(la ? A.ux : s.ux.x, lb ? B.ux : s.ux.y));
+    __stcs(reinterpret_cast<float2 *>(a.uy + pa), make_float2(la ? A.uy : s.uy.x, lb ? B.uy : s.uy.y));
     if (a.rec_cap > 0) {
         if (sa) a.rec_cnt[pa] = 0;
         if (sb) a.rec_cnt[pa + 1] = 0;
@@ -644,7 +658,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     while (qtail - qhead >= 32) {
         __syncwarp();
         const WalkItem w = q[(qhead + lane) & (P32_QUEUE2 - 1)];
-        walk_particle(a, w);
+        walk_particle<true>(a, w);
         qhead += 32;
         __syncwarp();
     }
@@ -678,7 +692,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
     const unsigned left = qtail - qhead;
     if (left > 0) {
         __syncwarp();
-        if ((unsigned)lane < left) walk_particle(a, q[(qhead + lane) & (P32_QUEUE2 - 1)]);
+        if ((unsigned)lane < left) walk_particle<true>(a, q[(qhead + lane) & (P32_QUEUE2 - 1)]);
     }
 }
 
