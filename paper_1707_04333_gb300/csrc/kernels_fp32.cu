@@ -615,21 +615,32 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     qtail += __popc(wa);
     if (B.walking) q[(qtail + __popc(wb & lt)) & (P32_QUEUE2 - 1)] = walk_item(pa + 1, s.fb, s.sp, s.l0.y, s.l1.y, B);
     qtail += __popc(wb);
-    // current of the particles that stay, Eq. (I.assign)
+    // current of the particles that stay, Eq. (I.assign).  The run of a thread's second
+    // particle is reduced across the warp; a first particle that ends a different run (an
+    // "orphan") is handed to the previous thread when that thread's second particle lies in
+    // the same triangle, and deposits with its own atomics otherwise.
     const bool same = A.key == B.key;
-    if (!same && A.key >= 0) {
+    const int key = B.key;
+    const int okey = same ? -1 : A.key;                  // orphan's triangle, -1: none
+    const int kp = __shfl_up_sync(full, key, 1);
+    const bool given = lane > 0 && okey >= 0 && okey == kp;
+    if (okey >= 0 && !given) {
         const int ew[3] = {__float_as_int(ra.r1.w), __float_as_int(ra.c1.z), __float_as_int(ra.c1.w)};
         add_seg32(a.ifix, ew, A.v);
     }
     int v0[3];
+    {
+        const bool taken = __shfl_down_sync(full, given, 1) && lane < 31;
 #pragma unroll
-    for (int m = 0; m < 3; ++m) v0[m] = B.v[m] + (same ? A.v[m] : 0);
-    const int key = B.key;
+        for (int m = 0; m < 3; ++m) {
+            const int on = __shfl_down_sync(full, A.v[m], 1);        // next thread's orphan
+            v0[m] = B.v[m] + (same ? A.v[m] : 0) + (taken ? on : 0);
+        }
+    }
     {
         const int kn = __shfl_down_sync(full, key, 1);
         const unsigned tails = __ballot_sync(full, (lane == 31) || (kn != key));
         const int seg_end = lane + __ffs(tails >> lane) - 1;
-        const int kp = __shfl_up_sync(full, key, 1);
         const bool head = (lane == 0) || (kp != key);
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
