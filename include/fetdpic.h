@@ -303,7 +303,7 @@ int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_ed
 
 /* Autotuner (no counterpart in the paper, which reports no kernels): times
  * short trials of every (FP32 particle-kernel variant in {2, ..., 12}) x (sort
- * interval in {8, 16, 32}) combination -- only the sort interval for FP64,
+ * interval in {8, 12, 16, 32}) combination -- only the sort interval for FP64,
  * nothing if sorting is off -- starting each from the current state, keeps
  * the fastest per step (sort cost included), and restores the particle and
  * field state exactly, so the simulation is unchanged: the trials record no

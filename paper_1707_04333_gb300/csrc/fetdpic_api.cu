@@ -1386,7 +1386,7 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     ctx->probe_n = 0;
     rc = copy_state(true);
     std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12} : std::vector<int>{3};
-    std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 16, 32};
+    std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 12, 16, 32};
     double best = 1e300;
     int bv = keep_variant, bs = keep_sort;
     cudaEvent_t t0, t1;
