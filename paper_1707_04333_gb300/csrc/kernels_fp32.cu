@@ -512,9 +512,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32(StepArgs32 a)
 // the state moves in 8-byte vector loads and stores.  When both particles of
 // a lane stay in the same triangle their currents are summed in the lane, so
 // the warp-segmented reduction runs once per 64 particles; a lane whose pair
-// straddles a change of triangle deposits its first particle with its own
-// integer atomics.  The per-particle arithmetic is process_chunk's, written out
-// the same way.
+// straddles a change of triangle hands its first particle to the previous
+// lane's run (or deposits it with its own integer atomics when that run is
+// another triangle's).  The walk rewrites a walker's momentum only after a
+// wall reflection, since this pass stores the pushed momentum of every live
+// particle.  The per-particle arithmetic is process_chunk's, written out the
+// same way.
 constexpr int P32_QUEUE2 = 128;              // walker ring per warp: 31 pending + 64 new fit
 
 struct PState2 { int fa, fb, sp; float2 l0, l1, ux, uy; };
