@@ -230,6 +230,24 @@ __device__ __forceinline__ int exit_edge(const float *lin, const float *g, float
     return best;
 }
 
+// Deposit of one sub-segment of a walk: the signed integer current of its entry
+// edge `min` gets the carry left by the previous sub-segment on the same edge,
+// and the current of its exit edge `best` is carried to the next sub-segment
+// instead of being deposited, so a crossed edge takes one atomic, not two.
+// Integer sums: the result does not depend on where the additions happen.
+__device__ __forceinline__ void add_walk32(unsigned long long *ifix, const int *ew, const int *v, int min,
+                                           int best, long long &carry)
+{
+    const long long cin = carry;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        long long s = (ew[m] & 1) ? -(long long)v[m] : (long long)v[m];
+        if (m == min) s += cin;
+        if (m == best) carry = s;
+        else atomicAdd(ifix + (ew[m] >> 1), (unsigned long long)s);
+    }
+}
+
 // Register-resident element k (0..2) of a 3-array (no dynamic indexing, so no local memory).
 template <typename T>
 __device__ __forceinline__ T sel3(const T *a, int k)
@@ -283,6 +301,7 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
     float lfin[3];
     float G[6];
     int ew[3], nb[3];
+    long long carry = 0;                          // current on the entry edge, not yet deposited
     load_cst(a.cst, f, G, ew, nb);
     for (;;) {
         float g[3];
@@ -297,7 +316,7 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
             lfin[1] = lin[1] + rem * g[1];
             lfin[2] = 1.f - lfin[0] - lfin[1];
             seg_current32(lin, lfin, wfix, v);
-            add_seg32(a.ifix, ew, v);
+            add_walk32(a.ifix, ew, v, min, -1, carry);
             break;
         }
         float lout[3];
@@ -305,11 +324,12 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
 #pragma unroll
         for (int k = 0; k < 3; ++k) lout[k] = (k == best) ? 0.f : lin[k] + dtau * g[k];
         seg_current32(lin, lout, wfix, v);
-        add_seg32(a.ifix, ew, v);
+        add_walk32(a.ifix, ew, v, min, best, carry);
         lin[0] = lout[0]; lin[1] = lout[1]; lin[2] = lout[2];
         tin = tb;
         const int eg = sel3(ew, best) >> 1;
         if (ncross >= a.max_cross) {
+            atomicAdd(a.ifix + eg, (unsigned long long)carry);
             lfin[0] = lin[0]; lfin[1] = lin[1]; lfin[2] = lin[2];
             atomicOr(a.status, (unsigned)ST_WALK);
             break;

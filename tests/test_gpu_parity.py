@@ -358,12 +358,13 @@ def test_edge_cases(fx):
     sim.close()
     # walk limit: fast particles with max_crossings = 1
     wf, _ = random_state(4, n_e=500, n_p=10, dt=3e-9)
-    sim = fetdpic.Simulation(wf, precision="fp64", max_crossings=1, sort_interval=-1).load()
-    fetdpic.fetdpic_step(sim.h, 1, "boris")
-    with pytest.raises(fetdpic.FetdpicError) as ei:
-        fetdpic.fetdpic_sync(sim.h)
-    assert ei.value.code == fetdpic.EWALK
-    sim.close()
+    for prec in ("fp64", "fp32"):
+        sim = fetdpic.Simulation(wf, precision=prec, max_crossings=1, sort_interval=-1).load()
+        fetdpic.fetdpic_step(sim.h, 1, "boris")
+        with pytest.raises(fetdpic.FetdpicError) as ei:
+            fetdpic.fetdpic_sync(sim.h)
+        assert ei.value.code == fetdpic.EWALK, prec
+        sim.close()
     # a triangle outside the mesh given to write_particles: found on the device, the particle dropped,
     # EINVAL at the next sync
     for prec in ("fp64", "fp32"):
