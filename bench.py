@@ -202,6 +202,14 @@ def run_reference(args):
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_particles32_pair200k_traffic.json")
 
 
+def kernel_label(variant):
+    """Name of the FP32 particle kernel a variant launches (0 = the library's default, which takes
+    two particles per thread)."""
+    two = variant == 0 or variant >= 8
+    return (f"{'k_particles32x2' if two else 'k_particles32'} (gather+push+walk+deposit, "
+            f"variant {variant if variant else 'default'})")
+
+
 def measured_traffic(workload, pbytes):
     """DRAM bytes (read + write) of one particle-kernel launch from the committed ncu summary, or
     None when the summary is for another workload or the kernel's sources changed since the
@@ -317,7 +325,7 @@ def main():
     traffic, traffic_note = measured_traffic(args.workload, pbytes)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": "k_particles32 (gather+push+walk+deposit)", "peak_kind": peak_kind,
+                "kernel": kernel_label(sim.tuned[0]), "peak_kind": peak_kind,
                 "bytes_per_launch": pbytes, "traffic_source": traffic_note}
     stages = {"faraday_ms": st[0] / max(st[3], 1), "particles_ms": part_ms,
               "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1),
