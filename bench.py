@@ -3,7 +3,8 @@
 
 One step = Faraday update (+ per-triangle field record), the fused
 gather / push / walk / deposit particle kernel, the Ampere update (C^T H b - i
-and the SPAI SpMV) and, every 16 steps, the counting sort by triangle.
+and the SPAI SpMV) and, every K steps (K autotuned), the counting sort by
+triangle.
 
 Workload (default): magnetized electron-positron pair plasma on a 200,978-
 triangle jittered Delaunay mesh with PEC walls, 20 particles per species per
