@@ -14,17 +14,21 @@ positions); the plain FP64 path runs the same workload beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-With N > 1 (torchrun, one rank per GPU) every rank advances its own replica
-(weak scaling), or, for the batched form, its share of the 64 instances split
-by estimated cost (strong scaling); no collective is on the data path, the
-time is the max over ranks and the value counts all ranks' particle-steps.
+With N > 1 (one rank per GPU; started through torch.distributed.run, which
+bench.py does itself when launched without it) every rank advances its own
+replica (weak scaling), or, for the batched form, its share of the 64
+instances split by estimated cost (strong scaling); no collective is on the
+data path, the time is the max over ranks and the value counts all ranks'
+particle-steps.  The headline is the median of 5 timed repeats of K steps.
 """
 from __future__ import annotations
 
 import argparse
 import json
 import math
+import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -37,6 +41,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (gather+push+walk+deposit), FP32/batched vs FP64 plain"
 UNIT = "particle-steps/s"
+CPU_SAMPLE = 250_000          # oracle particles per host process, in both CPU legs
+FP64_FLOP_PER_PARTICLE = 243.6  # FP64 flops per particle-step of the plain FP64 kernel (ncu count)
 
 
 def parse():
@@ -57,9 +63,15 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=1_000_000)
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE,
+                    help="particles of the oracle's sample per host process")
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle processes (0 = every host core)")
+    ap.add_argument("--repeats", type=int, default=5, help="timed repeats of K steps (median reported)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and high-gamma beam workloads of the default line")
     ap.add_argument("--variant", type=int, default=0, help="FP32 particle-kernel variant (0 = autotuned)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library defaults instead of autotuning")
+    ap.add_argument("--dry-ranks", action="store_true", help=argparse.SUPPRESS)
     a = ap.parse_args()
     a.pusher_given = a.pusher is not None
     if a.pusher is None:
@@ -149,33 +161,99 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": n}
 
 
-def cpu_oracle(w, sample, steps, warmup=0, seed=5, target_s=None):
-    """Time the FP64 oracle (single thread, as it stands) on a seeded sample of the workload's
-    particles: full steps (Faraday, particles, Ampere with the level-2 SPAI) on the full mesh.
-    With target_s, one calibration step sets the step count for about target_s seconds."""
+def host_cpu():
+    """CPU model, architecture and the cores this process may run on."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model or platform.processor() or "unknown", "arch": platform.machine(), "cores": cores}
+
+
+def _oracle_worker(job):
+    """One host process: the FP64 oracle as it stands (single-threaded) on one seeded particle
+    sample, full steps (Faraday, particles, Ampere with the level-2 SPAI) on the full mesh.
+    Returns (particles, seconds, steps); with target_s one calibration step sets the step count
+    for about target_s seconds."""
+    nodes, tris, dt, b0, e0, ext, species, pusher, warmup, steps, target_s = job
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
     from oracle import oracle
     from paper_1707_04333_gb300 import inputs
-    oracle.build()
-    sim = oracle.OracleSim(w.mesh.nodes, w.mesh.triangles, w.dt, eps0=inputs.EPS0, mu0=inputs.MU0,
-                           c=inputs.C_LIGHT, spai_level=2, b0=w.b0, e0=w.e0, ext=w.ext)
-    rng = np.random.default_rng(seed)
+    sim = oracle.OracleSim(nodes, tris, dt, eps0=inputs.EPS0, mu0=inputs.MU0, c=inputs.C_LIGHT, spai_level=2,
+                           b0=b0, e0=e0, ext=ext)
     n = 0
-    per = max(1, sample // len(w.species))
-    for s in w.species:
-        idx = np.sort(rng.choice(len(s.x), min(per, len(s.x)), replace=False))
-        sim.load(s.q, s.m, s.x[idx], s.u[idx], s.hint[idx])
-        n += len(idx)
+    for q, m, x, u, hint in species:
+        sim.load(q, m, x, u, hint)
+        n += len(x)
     for _ in range(warmup):
-        sim.step(w.pusher)
+        sim.step(pusher)
     if target_s:
         t0 = time.perf_counter()
-        sim.step(w.pusher)
+        sim.step(pusher)
         steps = int(max(2, min(200, target_s / max(time.perf_counter() - t0, 1e-3))))
     t0 = time.perf_counter()
     for _ in range(steps):
-        sim.step(w.pusher)
-    dt = time.perf_counter() - t0
-    return n * steps / dt, n, dt, steps
+        sim.step(pusher)
+    return n, time.perf_counter() - t0, steps
+
+
+def cpu_oracle(w, sample, steps, warmup=0, procs=1, target_s=None, seed=5):
+    """Time the oracle on `procs` host processes at once (spawned, so no GPU state is inherited),
+    each on its own seeded sample of `sample` particles (split over the species) with the full mesh
+    and field update.  Returns (rate, particles, seconds, steps): all processes' particle-steps per
+    second of the slowest process's step time; one process gives the single-core rate."""
+    from oracle import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    per = max(1, sample // len(w.species))
+    jobs = []
+    for _ in range(max(1, procs)):
+        sp = []
+        for s in w.species:
+            idx = np.sort(rng.choice(len(s.x), min(per, len(s.x)), replace=False))
+            sp.append((s.q, s.m, s.x[idx], s.u[idx], s.hint[idx]))
+        jobs.append((w.mesh.nodes, w.mesh.triangles, w.dt, w.b0, w.e0, w.ext, sp, w.pusher, warmup, steps,
+                     target_s))
+    if len(jobs) == 1:
+        res = [_oracle_worker(jobs[0])]
+    else:
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    n = sum(r[0] for r in res)
+    per_step = max(r[1] / r[2] for r in res)
+    nsteps = min(r[2] for r in res)
+    return n / per_step, n, per_step * nsteps, nsteps
+
+
+def cpu_baseline_record(w, args, steps=0, warmup=0, target_s=None):
+    """The oracle on every host core (one process per core) and on one core, same sample size per
+    process in both; the all-core figure is the value."""
+    host = host_cpu()
+    procs = args.cpu_procs or host["cores"]
+    v1, n1, t1, s1 = cpu_oracle(w, args.cpu_sample, steps, warmup=warmup, procs=1, target_s=target_s)
+    va, na, ta, sa = cpu_oracle(w, args.cpu_sample, steps, warmup=warmup, procs=procs, target_s=target_s)
+    return {"value": va, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": (f"{procs} host processes (one per core), each the single-threaded oracle on its own seeded "
+                       f"sample of {args.cpu_sample} of the {w.n_particles} particles, full "
+                       f"{len(w.mesh.triangles)}-triangle mesh and field update, {sa} steps"),
+            "single_core": {"value": v1, "particles": n1, "steps": s1, "seconds": t1},
+            "cpu": host}
 
 
 def run_reference(args):
@@ -184,20 +262,53 @@ def run_reference(args):
         return
     ws = workload(args)
     w = max(ws, key=lambda x: x.n_particles)
-    sample = 250_000
-    val, n, dt, _ = cpu_oracle(w, sample, args.steps, warmup=args.warmup)
+    cpu = cpu_baseline_record(w, args, steps=args.steps, warmup=args.warmup)
+    val = cpu["value"]
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * args.cpu_sample * cpu["cores"] / val,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": describe(ws, args, "fp64 CPU oracle"),
-                                        "sample_particles": n},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n} of {w.n_particles} particles, full mesh and field update, "
-                                   f"{args.steps} steps"},
+                                        "sample_particles_per_process": args.cpu_sample},
+        "cpu_baseline": cpu,
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def launcher_argv(argv, n, port):
+    """Command that runs this benchmark as n local ranks, one per GPU (torch.distributed.run)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *argv]
+
+
+def _free_port():
+    import socket
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def dry_ranks(args):
+    """--dry-ranks: the multi-rank host path without a GPU (gloo): the batched form's instances
+    split over the ranks by estimated cost, the end-of-run reductions, one JSON line from rank 0."""
+    import torch.distributed as dist
+    from paper_1707_04333_gb300 import inputs, ranks
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    ws = inputs.batched_pair_plasmas(n_inst=64, seed=5, scale=0.02)
+    costs = [ranks.instance_cost(x.n_particles, len(x.mesh.triangles)) for x in ws]
+    mine = ranks.shard_instances(costs, world)[rank]
+    units = ranks.sum_over_ranks(sum(ws[i].n_particles for i in mine))
+    slowest = ranks.max_over_ranks(float(rank + 1))
+    count = ranks.sum_over_ranks(len(mine))
+    if rank == 0:
+        print(json.dumps({"dry_ranks": True, "n_gpus": world, "instances": int(count),
+                          "particles": int(units), "max_over_ranks": slowest}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_particles32_pair200k_traffic.json")
@@ -232,10 +343,79 @@ def measured_traffic(workload, pbytes):
     return t["dram_bytes_per_launch"], f"ncu, one launch (variant {t['variant']}): {os.path.relpath(TRAFFIC_SUMMARY, ROOT)}"
 
 
+def timed_steps(fetdpic, sim, steps, warmup, pusher, stream, barrier, repeats=1):
+    """Warm-up, then `repeats` timed regions of exactly `steps` steps, each bracketed by a barrier
+    and a device synchronisation, timed with CUDA events on the context stream.  Returns the ms
+    of each region."""
+    import torch
+    sim.step(warmup, pusher).sync()
+    out = []
+    for _ in range(repeats):
+        barrier()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        fetdpic.fetdpic_step(sim.h, steps, pusher)
+        ev1.record(stream)
+        fetdpic.fetdpic_sync(sim.h)
+        torch.cuda.synchronize()
+        barrier()
+        out.append(ev0.elapsed_time(ev1))
+    return out
+
+
+def workload_line(fetdpic, ws, args, stream, barrier, name, steps, warmup, cache):
+    """Headline-style numbers of one more workload form: FP32 graph replay (median of 3), the
+    particle kernel's event-timed share and HBM fraction, and the plain FP64 path beside it."""
+    from paper_1707_04333_gb300 import ranks
+    pusher = args.pusher
+    sim = fetdpic.Simulation(ws, precision="fp32", spai_level=2, sort_interval=args.sort_interval,
+                             stream=stream, use_graphs=True)
+    sim.load()
+    tuned = sim.autotune(pusher, trial_steps=32, cache=cache)
+    ms = statistics.median(timed_steps(fetdpic, sim, steps, warmup, pusher, stream, barrier, repeats=3))
+    pbytes, npart = fetdpic.fetdpic_particle_bytes(sim.h)
+    sim.close()
+    st_sim = fetdpic.Simulation(ws, precision="fp32", spai_level=2, sort_interval=tuned[1], stream=stream,
+                                kernel_variant=tuned[0], time_stages=True)
+    st_sim.load()
+    timed_steps(fetdpic, st_sim, steps, warmup, pusher, stream, barrier)
+    st, _ = fetdpic.fetdpic_stage_times(st_sim.h)
+    st_sim.close()
+    part_ms = st[1] / max(st[3], 1)
+    peak, _ = peaks()
+    k64 = min(steps, 20)
+    sim64 = fetdpic.Simulation(ws, precision="fp64", spai_level=2, sort_interval=tuned[1], stream=stream,
+                               time_stages=True)
+    sim64.load()
+    ms64 = timed_steps(fetdpic, sim64, k64, min(warmup, 3), pusher, stream, barrier)[0]
+    st64, _ = fetdpic.fetdpic_stage_times(sim64.h)
+    sim64.close()
+    value = ranks.aggregate_rate(npart, steps, ms)
+    v64 = ranks.aggregate_rate(npart, k64, ms64)
+    return {"workload": describe(ws, argparse.Namespace(**{**vars(args), "workload": name}), "fp32"),
+            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "particles": npart, "triangles": sum(len(w.mesh.triangles) for w in ws), "instances": len(ws),
+            "tuning": {"kernel_variant": tuned[0], "sort_interval": tuned[1]},
+            "particle_kernel": {"ms": part_ms, "achieved_gbs": pbytes / (part_ms / 1e3) / 1e9 if part_ms > 0 else None,
+                                "frac_of_measured_hbm": pbytes / (part_ms / 1e3) / 1e9 / peak if part_ms > 0 else None},
+            "stages_ms_per_step": {"faraday_ms": st[0] / max(st[3], 1), "particles_ms": part_ms,
+                                   "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1)},
+            "fp64_plain": {"value": v64, "ms_per_step": ms64 / k64, "particles_ms": st64[1] / max(st64[3], 1),
+                           "speedup_fp32_over_fp64": value / v64}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: start the ranks ourselves
+        sys.exit(subprocess.call(launcher_argv(sys.argv[1:], args.gpus, _free_port())))
+    if args.dry_ranks:
+        dry_ranks(args)
         return
     import torch
     import torch.distributed as dist
@@ -266,38 +446,7 @@ def main():
         ws = [ws[i] for i in ranks.shard_instances(costs, world)[rank]]
     w = max(ws, key=lambda x: x.n_particles)     # the instance the CPU baseline samples
     stream = torch.cuda.Stream()          # explicit stream: the context's kernels and the timing events
-
-    def timed_run(precision, steps, warmup, stages, graphs, tuned=None):
-        """Timed steps on the context stream.  graphs: replay captured one-step graphs (the
-        headline: no launch gaps, no stage events); stages: plain launches with CUDA events between
-        stages (the stage breakdown and the particle kernel's own time)."""
-        sim = fetdpic.Simulation(ws, precision=precision, spai_level=2,
-                                 sort_interval=tuned[1] if tuned else args.sort_interval,
-                                 time_stages=stages, stream=stream,
-                                 kernel_variant=tuned[0] if tuned else args.variant, use_graphs=graphs)
-        sim.load()
-        if tuned is None and args.variant == 0 and not args.no_tune:
-            tuned = sim.autotune(args.pusher, trial_steps=32,
-                                 cache=os.path.join(ROOT, "paper_1707_04333_gb300", "_build", "tuning.json"))
-        elif tuned is None:
-            tuned = (args.variant, args.sort_interval)
-        sim.tuned = tuned
-        sim.step(warmup, args.pusher).sync()
-        fetdpic.fetdpic_stage_times(sim.h)            # reset the sums
-        barrier()
-        torch.cuda.synchronize()
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        fetdpic.fetdpic_step(sim.h, steps, args.pusher)
-        ev1.record(stream)
-        fetdpic.fetdpic_sync(sim.h)
-        torch.cuda.synchronize()
-        barrier()
-        ms = ev0.elapsed_time(ev1)
-        st, launches = fetdpic.fetdpic_stage_times(sim.h)
-        pbytes, npart = fetdpic.fetdpic_particle_bytes(sim.h)
-        return sim, ms, st, launches, pbytes, npart
+    cache = os.path.join(ROOT, "paper_1707_04333_gb300", "_build", "tuning.json")
 
     dev_id = local
     try:
@@ -308,25 +457,41 @@ def main():
         pass
     clocks = ClockSampler(dev_id)
 
-    # ---- headline: FP32 path, steps replayed from captured graphs
+    # ---- headline: FP32 path, steps replayed from captured graphs, median of the repeats
+    sim = fetdpic.Simulation(ws, precision="fp32", spai_level=2, sort_interval=args.sort_interval, stream=stream,
+                             kernel_variant=args.variant, use_graphs=True)
+    sim.load()
+    if args.variant == 0 and not args.no_tune:
+        tuned = sim.autotune(args.pusher, trial_steps=32, cache=cache)
+    else:
+        tuned = (args.variant, args.sort_interval)
+    fetdpic.fetdpic_stage_times(sim.h)                # launch counts start here
     clocks.start()
-    sim, ms, _, launches, pbytes, npart = timed_run("fp32", args.steps, args.warmup, stages=False, graphs=True)
+    reps = timed_steps(fetdpic, sim, args.steps, args.warmup, args.pusher, stream, barrier, repeats=args.repeats)
     clk = clocks.stop()
-    ms = ranks.max_over_ranks(ms, device="cuda")
+    _, launches = fetdpic.fetdpic_stage_times(sim.h)
+    launches_per_region = launches * args.steps // max(1, args.steps * args.repeats + args.warmup)
+    reps = [ranks.max_over_ranks(x, device="cuda") for x in reps]
+    ms = statistics.median(reps)
+    pbytes, npart = fetdpic.fetdpic_particle_bytes(sim.h)
     npart_all = ranks.sum_over_ranks(npart, device="cuda")
-    # ---- the same workload and tuning with CUDA events between stages (breakdown, roofline)
-    ks = min(args.steps, 500)
-    sim_st, ms_st, st, _, _, _ = timed_run("fp32", ks, args.warmup, stages=True, graphs=False, tuned=sim.tuned)
-    sim_st.close()
     K = args.steps
     value = ranks.aggregate_rate(npart_all, K, ms)
+    # ---- the same workload and tuning with CUDA events between stages (breakdown, roofline)
+    ks = min(args.steps, 500)
+    sim_st = fetdpic.Simulation(ws, precision="fp32", spai_level=2, sort_interval=tuned[1], stream=stream,
+                                kernel_variant=tuned[0], time_stages=True)
+    sim_st.load()
+    ms_st = timed_steps(fetdpic, sim_st, ks, args.warmup, args.pusher, stream, barrier)[0]
+    st, _ = fetdpic.fetdpic_stage_times(sim_st.h)
+    sim_st.close()
     part_ms = st[1] / max(st[3], 1) if st[3] > 0 else 0.0
     peak, peak_kind = peaks()
     achieved = pbytes / (part_ms / 1e3) / 1e9 if part_ms > 0 else None
     traffic, traffic_note = measured_traffic(args.workload, pbytes)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "kernel": kernel_label(sim.tuned[0]), "peak_kind": peak_kind,
+                "kernel": kernel_label(tuned[0]), "peak_kind": peak_kind,
                 "bytes_per_launch": pbytes, "traffic_source": traffic_note}
     stages = {"faraday_ms": st[0] / max(st[3], 1), "particles_ms": part_ms,
               "ampere_ms": st[2] / max(st[3], 1), "sort_ms_per_step": st[4] / max(st[3], 1),
@@ -364,32 +529,56 @@ def main():
         te = ranks.max_over_ranks(te, device="cuda")
         e2e = {"value": ranks.aggregate_rate(npart_all, ke, te * 1e3), "unit": UNIT, "h2d_bytes_per_step": int(npart * 36),
                "d2h_bytes_per_step": int(npart * 36), "steps": ke}
-    sim_tuned = sim.tuned
     sim.close()
     del sim
+
+    # ---- measured arithmetic peaks (the FP64 path is bound by the FP64 rate)
+    arith = None
+    if rank == 0:
+        arith = {"fp32_tflops": fetdpic.fetdpic_fma_rate(False), "fp64_tflops": fetdpic.fetdpic_fma_rate(True),
+                 "how": "FMA chains filling every SM, CUDA events, best launch of >= 20 ms"}
 
     # ---- plain FP64 path on the same workload
     fp64 = None
     if not args.no_fp64:
         k64 = args.fp64_steps or min(args.steps, 100)
-        sim64, ms64, st64, l64, pb64, np64 = timed_run("fp64", k64, min(args.warmup, 3), stages=True,
-                                                       graphs=False, tuned=(3, sim_tuned[1]))
+        sim64 = fetdpic.Simulation(ws, precision="fp64", spai_level=2, sort_interval=tuned[1], stream=stream,
+                                   time_stages=True)
+        sim64.load()
+        ms64 = timed_steps(fetdpic, sim64, k64, min(args.warmup, 3), args.pusher, stream, barrier)[0]
+        st64, _ = fetdpic.fetdpic_stage_times(sim64.h)
+        pb64, np64 = fetdpic.fetdpic_particle_bytes(sim64.h)
+        sim64.close()
         ms64 = ranks.max_over_ranks(ms64, device="cuda")
         v64 = ranks.aggregate_rate(ranks.sum_over_ranks(np64, device="cuda"), k64, ms64)
         p64 = st64[1] / max(st64[3], 1)
         fp64 = {"value": v64, "ms_per_step": ms64 / k64, "steps": k64, "particles_ms": p64,
                 "particle_kernel_gbs": pb64 / (p64 / 1e3) / 1e9 if p64 > 0 else None,
-                "speedup_fp32_over_fp64": value / v64}
-        sim64.close()
+                "speedup_fp32_over_fp64": value / v64,
+                "note": "the FP64 path is the bit-exact reference: no FMA contraction, IEEE division and "
+                        "square root, so part of the speed-up is that choice"}
+        if arith and p64 > 0:
+            tf = FP64_FLOP_PER_PARTICLE * np64 / (p64 / 1e3) / 1e12
+            fp64["particle_kernel_fp64_tflops"] = tf
+            fp64["frac_of_measured_fp64"] = tf / arith["fp64_tflops"] if arith["fp64_tflops"] else None
+
+    # ---- the batched (64 uneven instances) and high-gamma beam forms, N = 1 only
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "pair":
+        extra = {}
+        for name in ("batched", "beam"):
+            a2 = argparse.Namespace(**{**vars(args), "workload": name, "pusher_given": False})
+            ws2 = workload(a2)
+            try:
+                extra[name] = workload_line(fetdpic, ws2, a2, stream, barrier, name, args.steps, args.warmup, cache)
+            except Exception as ex:          # report, do not lose the headline
+                extra[name] = {"error": f"{type(ex).__name__}: {ex}"}
+            del ws2
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, n, dt, ns = cpu_oracle(w, args.cpu_sample, 0, target_s=15.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n} of {w.n_particles} particles (seeded) of the largest instance, full "
-                         f"{len(w.mesh.triangles)}-triangle mesh "
-                         f"and field update, {ns} steps, {dt:.1f} s"}
+        cpu = cpu_baseline_record(w, args, steps=0, warmup=0, target_s=12.0)
 
     if rank == 0:
         line = {
@@ -398,18 +587,21 @@ def main():
             "scaling": "strong" if sharded else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": describe(ws, args, "fp32 cell-local barycentric"),
-                       "tuning": {"kernel_variant": sim_tuned[0], "sort_interval": sim_tuned[1]},
+                       "tuning": {"kernel_variant": tuned[0], "sort_interval": tuned[1]},
                        "triangles": sum(len(x.mesh.triangles) for x in ws), "particles_per_gpu": npart,
                        "instances": len(ws),
                        "l2": f"inputs larger than L2 (particle state 2 x {pbytes / 2e6:.0f} MB per step, L2 129 MB)",
                        "parallelism": (f"instances sharded over {world} ranks" if sharded
                                        else f"replicas x{world}")},
+            "repeats_ms": reps,
             "roofline": roofline,
             "stages_ms_per_step": stages,
             "fp64_plain": fp64,
+            "arith_peaks": arith,
+            "workloads": extra,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches_per_region),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -30,7 +30,8 @@
  *     error, fetdpic_last_error() returns a one-line description.  Device
  *     faults found by the kernels (walk limit, non-finite momentum) are
  *     latched in a device status word and returned by the next
- *     fetdpic_sync / fetdpic_read / fetdpic_check.
+ *     fetdpic_sync / fetdpic_read / fetdpic_check, which clear it: each
+ *     latched fault is reported once.
  *   - A context is bound to the CUDA device current at fetdpic_create and to
  *     one CUDA stream; calls on one context are not thread-safe.
  *   - Edges: unless given by the caller, the edges of an instance are all
@@ -82,7 +83,10 @@ typedef enum {
     FETDPIC_FP64 = 0,
     /* FP32 gather/push/deposit with cell-local barycentric positions and
      * momenta in units of c; FP64 for the Lorentz factor and momentum update
-     * of particles with gamma > 10, for the field update and the checks. */
+     * of particles with gamma > 10, for the field unknowns e, b, the Faraday
+     * update, C^T [*mu^-1] b - i and the checks.  The SPAI product dt M r of
+     * the Ampere update runs in FP32 (FP32 matrix values, r rounded to FP32,
+     * FP32 sums) and is added to the FP64 e. */
     FETDPIC_FP32 = 1
 } fetdpic_precision;
 
@@ -108,12 +112,16 @@ typedef struct {
                                 particles per thread: 8 = 256-thread blocks, 9 = 128, 10 = 64;
                                 11 = 128 and 12 = 64 with the two particles' triangle records read
                                 one after the other (fewer registers, 24 warps per SM).
-                                0 = default (11).  All give identical results. */
+                                0 = default (10).  All give identical results. */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);
     void (*dev_free)(void *ptr, void *user);
     void *alloc_user;
+    long long wait_spin_limit; /* polls of each bounded wait inside a kernel (variant 5's staged
+                                copies) before it gives up and reports FETDPIC_ETIMEOUT;
+                                0 = 2^20; negative = no poll, every such wait gives up at
+                                once (exercises the timeout path) */
 } fetdpic_params;
 
 /* One simulation instance (mesh + fields).  Instances share nothing but the
@@ -156,7 +164,9 @@ int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *p, int n_inst, const
 
 /* Add one species of n superparticles (charge q, rest mass m) to instance
  * `inst`.  x: [n][2] positions (m); u: [n][2] momenta u = gamma v (m/s),
- * taken as u^{n-1/2} (no half-step back-push).  cell_hint: optional [n]
+ * taken as u^{n-1/2} (no half-step back-push): the leapfrog of Eq.
+ * (eq.motion.dis) staggers u by half a step against r, and the paper does not
+ * say how a loaded state is staggered.  cell_hint: optional [n]
  * triangle indices to try first (a particle goes to the hint when all its
  * barycentric coordinates there are >= 0, else to the lowest-index triangle
  * where they are).  Returns the new species id (>= 0), or FETDPIC_EOUTSIDE if
@@ -181,15 +191,24 @@ int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const double *x, cons
 int fetdpic_write_fields(fetdpic_ctx *ctx, int inst, const double *e, const double *b);
 
 /* Enqueue nsteps time steps with pusher `pusher` (fetdpic_pusher) on the
- * context stream.  Asynchronous: returns after the launches. */
+ * context stream.  One step is the cycle of Sec. II.A-II.D in the order of
+ * the list at the top of this header: Faraday (Eq. (semi.dis.curl.1)),
+ * gather (Sec. II.B), push (Sec. II.C), move and walk (Eq.
+ * (eq.motion.dis)), deposit (Eq. (I.assign)), Ampere (Eq.
+ * (semi.dis.curl.2)); then, every sort_interval steps, the counting sort by
+ * triangle (not in the paper).  Asynchronous: returns after the launches;
+ * device faults are reported by the next fetdpic_sync. */
 int fetdpic_step(fetdpic_ctx *ctx, long long nsteps, int pusher);
 
-/* Wait for the context stream; return the first latched device status. */
+/* Wait for the context stream; return the latched device status (walk
+ * limit, non-finite momentum, bounded-wait timeout, bad written triangle) of
+ * the steps since the last report, then clear it. */
 int fetdpic_sync(fetdpic_ctx *ctx);
 
-/* Copy state of instance `inst` to host buffers (each may be NULL):
- * e [n_edges] = e^n, b [n_tri] = b^{n-1/2} (the latest face DoFs),
- * j [n_edges] = i^{n-1/2} of the last step.  Then species `species` (ignored
+/* Copy state of instance `inst` to host buffers (each may be NULL), in the
+ * staggering of the leapfrog (Sec. II.A, Eq. (eq.motion.dis)): e [n_edges] =
+ * e^n, b [n_tri] = b^{n-1/2} (the latest face DoFs), j [n_edges] = i^{n-1/2}
+ * of the last step (Eq. (I.assign)).  Then species `species` (ignored
  * if x, u and cell are all NULL): x [n][2], u [n][2], cell [n], in load
  * order.  FP32 mode converts barycentric positions to x = sum_k l_k r_k. */
 int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
@@ -197,25 +216,42 @@ int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
 
 /* Same particle output as fetdpic_read (x, u, cell of species `species`, load
  * order, FP32 positions converted), for callers that cannot allocate device
- * memory at the time of the call: code running while a stream is being
- * captured (allocation calls are not allowed there), real-time loops that
- * forbid allocator latency, plug-ins whose host framework owns all device
- * memory.  fetdpic_read allocates its device staging buffer on first use;
- * this call stages through a fixed array compiled into the library instead
- * (9 MiB = 262,144 particles x 36 B; every GPU that loads the library holds
- * it until the process exits) and calls no allocation routine.
+ * memory at the time of the call: real-time loops that forbid allocator
+ * latency, plug-ins whose host framework owns all device memory.
+ * fetdpic_read allocates its device staging buffer on first use; this call
+ * stages through a fixed array compiled into the library instead (9 MiB =
+ * 262,144 particles x 36 B; every GPU that loads the library holds it until
+ * the process exits) and calls no allocation routine.  Like fetdpic_read it
+ * waits for the context stream before it returns.
  *   - The paper has no counterpart: this is an interface convenience.
  *   - Species with more than 262,144 particles are rejected (FETDPIC_EINVAL,
- *     the count in fetdpic_last_error); the context must have run
- *     fetdpic_step or fetdpic_read once (FETDPIC_ESTATE otherwise).
+ *     the count in fetdpic_last_error).  The particles must already be on
+ *     the device (moving them there allocates): after fetdpic_step,
+ *     fetdpic_write_particles, fetdpic_autotune or a fetdpic_read with a
+ *     particle buffer; FETDPIC_ESTATE otherwise.
  *   - The first call on each device looks up the array's device address
- *     (with that device current); make that first call before any stream
- *     capture.
- *   - All calls share the one array and every call rewrites the slots it
- *     reads, so nothing needs clearing; calls that overlap on the GPU (other
- *     threads, other contexts on other streams) race on it.
+ *     (with that device current).
+ *   - All calls share the one array.  Each call first sets the slots it uses
+ *     to all-one bytes, so a particle dropped by fetdpic_write_particles (a
+ *     triangle outside the mesh, reported as FETDPIC_EINVAL) reads NaN
+ *     position and momentum and triangle -1, never an earlier call's data.
+ *     Calls that overlap on the GPU (other threads, other contexts on other
+ *     streams) race on the array.
  * x [n][2], u [n][2], cell [n] are host buffers, each may be NULL. */
 int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell);
+
+/* Nodal charge of the current particle state of instance `inst`, Eq.
+ * (scatter.charge.assign): q_i = sum_p Q_p lambda_i(r_p) over the particles of
+ * the instance, each particle's three barycentric weights rounded to the
+ * fixed-point quantum of the instance before the integer sum (the same
+ * arithmetic as the continuity and Gauss-law checks).  q [n_nodes] host
+ * buffer (C per unit depth; NULL = only the quantum); *quantum (may be NULL)
+ * = the charge of one fixed-point unit, so q / quantum are exact integers.
+ * With periodic walls the charge of an image node lands on its partner and
+ * the image reads 0.  Allocates a device buffer of 8 B per node on the first
+ * call; synchronous.  Before the first step it moves the loaded particles to
+ * the device like fetdpic_step does. */
+int fetdpic_read_charge(fetdpic_ctx *ctx, int inst, double *q, double *quantum);
 
 /* Crossed-edge record of the last step for species `species` (needs
  * record_walk > 0): cnt [n] crossings per particle; rec [n][record_walk]
@@ -328,6 +364,14 @@ int fetdpic_stage_times(fetdpic_ctx *ctx, double out[6], long long *launches);
  * and written: FP64 2 x 36 B, FP32 2 x 20 B per particle) and the particle
  * count; the roofline numerator. */
 int fetdpic_particle_bytes(fetdpic_ctx *ctx, double *bytes, long long *n_particles);
+
+/* Measurement aid, no counterpart in the paper: the FP32 (fp64 = 0) or FP64
+ * (fp64 = 1) fused multiply-add rate of the current device in TFLOP/s, from
+ * CUDA-event-timed launches of independent FMA chains filling every SM (best
+ * of the launches that ran >= 20 ms; about 0.2 s in all).  It is the
+ * denominator of the arithmetic roofline of the FP64 particle path, which the
+ * FP64 rate bounds.  Needs no context; runs on a stream of its own. */
+int fetdpic_fma_rate(int fp64, double *tflops);
 
 const char *fetdpic_last_error(const fetdpic_ctx *ctx);
 

@@ -48,7 +48,8 @@ struct fetdpic_ctx {
     long long nfree = 0;
 
     // device: mesh and fields
-    Geo64 *geo64 = nullptr; Cst32 *cst32 = nullptr; double2 *dtinv = nullptr; Topo *topo = nullptr;
+    Geo64 *geo64 = nullptr; double2 *dtinv = nullptr; Topo *topo = nullptr;
+    CstA *csta = nullptr; CstB *cstb = nullptr;
     Rec64 *rec64 = nullptr; Rec32 *rec32 = nullptr;
     double *e = nullptr, *b = nullptr, *d = nullptr, *r = nullptr, *j = nullptr;
     unsigned long long *ifix = nullptr;
@@ -60,6 +61,8 @@ struct fetdpic_ctx {
     unsigned *status = nullptr;
     std::vector<double> unit_host;           // per instance (q_ref/dt) / scale
     std::vector<double> fixscale;            // per instance fixed-point scale (2^shift in FP64)
+    std::vector<double> qunit_host;          // per instance charge of one fixed-point unit: q_ref / scale
+    unsigned long long *qread = nullptr;     // nodal charge for fetdpic_read_charge (allocated on first use)
 
     // particles
     std::vector<StagedSpecies> staged;
@@ -192,6 +195,17 @@ static int map_status(fetdpic_ctx *ctx, unsigned st)
     return FETDPIC_OK;
 }
 
+// Reads the device status word and clears it when set, so a latched fault is
+// reported once; returns the mapped status (the caller's stream must be idle).
+static int take_status(fetdpic_ctx *ctx)
+{
+    if (!ctx->status) return FETDPIC_OK;
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (st) CK(cudaMemset(ctx->status, 0, sizeof(unsigned)));
+    return map_status(ctx, st);
+}
+
 extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int n_inst, const fetdpic_instance *inst)
 {
     if (!out) return FETDPIC_EINVAL;
@@ -212,9 +226,9 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.block_size < 32 || P.block_size > 256 || (P.block_size & 31) || (SPECIES_ALIGN % P.block_size))
         return FETDPIC_EINVAL;
     if (P.record_walk < 0) return FETDPIC_EINVAL;
-    // untuned FP32 default: two particles per thread in 128-thread blocks, records read one
-    // particle at a time (24 warps per SM at 80 registers), measured fastest on the benchmark workload
-    if (P.kernel_variant == 0) P.kernel_variant = 11;
+    // untuned FP32 default: two particles per thread in 64-thread blocks (20 warps per SM at 96
+    // registers), measured fastest on the benchmark workload
+    if (P.kernel_variant == 0) P.kernel_variant = 10;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
     if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
@@ -253,7 +267,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
 
     // ---- host images of the device tables
     std::vector<Geo64> g64(ctx->F);
-    std::vector<Cst32> g32(P.precision == FETDPIC_FP32 ? ctx->F : 0);
+    std::vector<CstA> g32(P.precision == FETDPIC_FP32 ? ctx->F : 0);
+    std::vector<CstB> g32b(g32.size());
     std::vector<double2> dti(P.precision == FETDPIC_FP32 ? ctx->F : 0);
     std::vector<Topo> tp(ctx->F);
     std::vector<double> e0(ctx->E, 0.0), b0(ctx->F, 0.0), d0(ctx->E, 0.0);
@@ -289,13 +304,14 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             T.inst = k;
             b0[co + f] = I.b0 * (0.5 * M.d2A[f]);          // b_f = B0 A_f
             if (!g32.empty()) {
-                Cst32 &H = g32[co + f];
-                for (int m = 0; m < 3; ++m) {
+                CstA &H = g32[co + f];
+                for (int m = 0; m < 2; ++m) {
                     H.G[2 * m] = (float)(P.c * I.dt * M.gx[3 * f + m]);
                     H.G[2 * m + 1] = (float)(P.c * I.dt * M.gy[3 * f + m]);
-                    H.nb[m] = T.nb[m];
                 }
-                H.ew0 = T.ew[0]; H.ew1 = T.ew[1]; H.ew2 = T.ew[2];
+                H.ew1 = T.ew[1]; H.ew2 = T.ew[2];
+                H.nb0 = T.nb[0]; H.nb1 = T.nb[1];
+                g32b[co + f] = CstB{T.ew[0], T.nb[2]};
                 dti[co + f] = make_double2(I.dt, M.inv2A[f]);
             }
         }
@@ -400,7 +416,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     try {
         ctx->geo64 = ctx->alloc<Geo64>(ctx->F);
         if (P.precision == FETDPIC_FP32) {
-            ctx->cst32 = ctx->alloc<Cst32>(ctx->F);
+            ctx->csta = ctx->alloc<CstA>(ctx->F);
+            ctx->cstb = ctx->alloc<CstB>(ctx->F);
             ctx->dtinv = ctx->alloc<double2>(ctx->F);
             ctx->rec32 = ctx->alloc<Rec32>(ctx->F);
         } else {
@@ -465,7 +482,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         CK(cudaMemsetAsync(ctx->chk_out, 0, sizeof(double) * 3 * n_inst, ctx->stream));
     }
     rc = rc ? rc : upload(ctx, ctx->geo64, g64.data(), g64.size());
-    if (!g32.empty()) rc = rc ? rc : upload(ctx, ctx->cst32, g32.data(), g32.size());
+    if (!g32.empty()) rc = rc ? rc : upload(ctx, ctx->csta, g32.data(), g32.size());
+    if (!g32b.empty()) rc = rc ? rc : upload(ctx, ctx->cstb, g32b.data(), g32b.size());
     if (!dti.empty()) rc = rc ? rc : upload(ctx, ctx->dtinv, dti.data(), dti.size());
     rc = rc ? rc : upload(ctx, ctx->topo, tp.data(), tp.size());
     rc = rc ? rc : upload(ctx, ctx->e, e0.data(), e0.size());
@@ -508,6 +526,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     CK(cudaMemsetAsync(ctx->status, 0, sizeof(unsigned), ctx->stream));
     ctx->unit_host.assign(n_inst, 0.0);
     ctx->fixscale.assign(n_inst, 1.0);
+    ctx->qunit_host.assign(n_inst, 0.0);
     CK(cudaStreamSynchronize(ctx->stream));
     *out = holder.release();
     return FETDPIC_OK;
@@ -599,6 +618,7 @@ static int finalize(fetdpic_ctx *ctx)
         ctx->fixscale[k] = P.precision == FETDPIC_FP32 ? FP32_SCALE : std::ldexp(1.0, sh);
         const double qr = qref[k] > 0 ? qref[k] : 1.0;
         ctx->unit_host[k] = (qr / ctx->inst[k].dt) / ctx->fixscale[k];
+        ctx->qunit_host[k] = qr / ctx->fixscale[k];
     }
     ctx->sp.resize(ns);
     long long off = 0, packed = 0, hist_n = 0;
@@ -635,6 +655,8 @@ static int finalize(fetdpic_ctx *ctx)
     }
     ctx->P = off;
     ctx->nblocks = off / ctx->block;
+    if (P.record_walk > 0 && off >= (1ll << 31))
+        return ctx->fail(FETDPIC_EINVAL, "record_walk needs fewer than 2^31 particle slots");
     ctx->hist_n = hist_n;
     const bool f32 = P.precision == FETDPIC_FP32;
     const size_t fb = f32 ? 4 : 8;
@@ -645,7 +667,7 @@ static int finalize(fetdpic_ctx *ctx)
         // the FP32 path takes the applied fields from the per-triangle field record
         T.kappa = D.kappa; T.xe_x = 0.0f; T.xe_y = 0.0f; T.xb = 0.0f;
         T.wfix = (float)D.wfix;
-        T.inst = D.inst; T.edge_off = ctx->edge_off[D.inst]; T.pad = 0;
+        T.inst = D.inst; T.edge_off = ctx->edge_off[D.inst]; T.off = (int)D.off;
     }
     try {
         ctx->sp32_dev = ctx->alloc<Sp32>(s32.size());
@@ -716,9 +738,7 @@ static int finalize(fetdpic_ctx *ctx)
     rc = rc ? rc : upload(ctx, ctx->pad_adj, pad_adj.data(), pad_adj.size());
     rc = rc ? rc : upload(ctx, ctx->inst_unit, ctx->unit_host.data(), ctx->unit_host.size());
     if (ctx->qunit) {
-        std::vector<double> qu(ni);
-        for (int k = 0; k < ni; ++k) qu[k] = (qref[k] > 0 ? qref[k] : 1.0) / ctx->fixscale[k];
-        rc = rc ? rc : upload(ctx, ctx->qunit, qu.data(), qu.size());
+        rc = rc ? rc : upload(ctx, ctx->qunit, ctx->qunit_host.data(), ctx->qunit_host.size());
     }
     if (rc) return rc;
     if (ctx->rec_cnt) CK(cudaMemsetAsync(ctx->rec_cnt, 0, sizeof(int) * ctx->P, ctx->stream));
@@ -738,7 +758,7 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
     a.cell = ctx->cell;
     a.ifix = ctx->ifix; a.status = ctx->status;
     a.max_cross = ctx->p.max_crossings;
-    a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec;
+    a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec; a.id = ctx->id;
     a.edge_off = ctx->edge_off_dev;
     a.nblocks = ctx->nblocks; a.block = ctx->block;
     a.tshift = ctx->tshift; a.period = ctx->period;
@@ -749,16 +769,19 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
 static StepArgs32 args32(fetdpic_ctx *ctx)
 {
     StepArgs32 a{};
-    a.cst = ctx->cst32; a.rec = ctx->rec32;
+    a.csta = ctx->csta; a.cstb = ctx->cstb; a.rec = ctx->rec32;
     a.sp = ctx->sp32_dev; a.chunk_sp = ctx->chunk_sp; a.nchunks = ctx->P / 32;
     a.variant = ctx->p.kernel_variant;
     a.l0 = (float *)ctx->f[0]; a.l1 = (float *)ctx->f[1]; a.ux = (float *)ctx->f[2]; a.uy = (float *)ctx->f[3];
     a.cell = ctx->cell;
     a.ifix = ctx->ifix; a.status = ctx->status;
     a.max_cross = ctx->p.max_crossings;
-    a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec;
+    a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec; a.id = ctx->id;
     a.edge_off = ctx->edge_off_dev;
     a.nblocks = ctx->nblocks; a.block = ctx->block;
+    // polls per bounded wait: 0 = 2^20; negative = none (the wait gives up at once)
+    const long long lim = ctx->p.wait_spin_limit;
+    a.spin = lim > 0 ? (unsigned)std::min<long long>(lim, 1ll << 30) : (lim < 0 ? 0u : (1u << 20));
     return a;
 }
 
@@ -820,7 +843,7 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
             x.finst = ctx->face_inst; x.ext = ctx->ext_dev; x.amp = ctx->ext_amp; x.extw = ctx->extw;
             x.half_over_c = 0.5 / ctx->p.c;
         }
-        launch_faraday32(ctx->stream, ctx->F, ctx->cst32, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
+        launch_faraday32(ctx->stream, ctx->F, ctx->csta, ctx->cstb, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
                          (float)(0.5 / (ctx->p.c * ctx->p.c)), x);
     }
     else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
@@ -951,10 +974,8 @@ extern "C" int fetdpic_sync(fetdpic_ctx *ctx)
 {
     if (!ctx) return FETDPIC_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
-    unsigned st = 0;
-    if (ctx->status) CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     collect_events(ctx);
-    return map_status(ctx, st);
+    return take_status(ctx);
 }
 
 // Reusable device scratch for particle-state transfers (grown on demand).
@@ -1127,9 +1148,31 @@ extern "C" int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, do
             CK(cudaStreamSynchronize(ctx->stream));
         }
     }
-    unsigned st = 0;
-    if (ctx->status) CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    return map_status(ctx, st);
+    return take_status(ctx);
+}
+
+extern "C" int fetdpic_read_charge(fetdpic_ctx *ctx, int inst, double *q, double *quantum)
+{
+    if (!ctx || inst < 0 || inst >= (int)ctx->mesh.size()) return FETDPIC_EINVAL;
+    int rc = finalize(ctx);
+    if (rc) return rc;
+    CK(cudaSetDevice(ctx->device));
+    if (quantum) *quantum = ctx->qunit_host[inst];
+    if (!q) return FETDPIC_OK;
+    if (!ctx->qread) {
+        try { ctx->qread = ctx->alloc<unsigned long long>(std::max(ctx->N, 1)); }
+        catch (const std::bad_alloc &) { return FETDPIC_ENOMEM; }
+    }
+    charge_now(ctx, ctx->qread);
+    CK(cudaGetLastError());
+    const int nn = ctx->mesh[inst].nn;
+    std::vector<unsigned long long> v(nn);
+    CK(cudaMemcpyAsync(v.data(), ctx->qread + ctx->node_off[inst], sizeof(unsigned long long) * nn,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double qu = ctx->qunit_host[inst];
+    for (int n = 0; n < nn; ++n) q[n] = (double)(long long)v[n] * qu;
+    return FETDPIC_OK;
 }
 
 extern "C" int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *rec)
@@ -1141,24 +1184,11 @@ extern "C" int fetdpic_read_walk(fetdpic_ctx *ctx, int species, int *cnt, int *r
     if (species < 0 || species >= (int)ctx->sp.size()) return FETDPIC_EINVAL;
     const Species &D = ctx->sp[species];
     if (D.n == 0) return FETDPIC_OK;
-    int *oc = nullptr, *orc = nullptr;
-    try {
-        oc = ctx->alloc<int>(D.n);
-        orc = ctx->alloc<int>((size_t)D.n * ctx->p.record_walk);
-    } catch (const std::bad_alloc &) {
-        return FETDPIC_ENOMEM;
-    }
-    launch_unsort_rec(ctx->stream, D.off, D.cap, ctx->id, ctx->cell, ctx->rec_cnt, ctx->rec, ctx->p.record_walk, oc, orc);
-    CK(cudaGetLastError());
+    // the kernels write the record at species storage offset + load index: already in load order
+    const size_t rc_ = (size_t)ctx->p.record_walk;
     CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemcpy(cnt, oc, sizeof(int) * D.n, cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(rec, orc, sizeof(int) * D.n * ctx->p.record_walk, cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 2; ++k) {
-        void *q = ctx->allocs.back();
-        ctx->allocs.pop_back();
-        if (ctx->p.dev_free) ctx->p.dev_free(q, ctx->p.alloc_user);
-        else cudaFree(q);
-    }
+    CK(cudaMemcpy(cnt, ctx->rec_cnt + D.off, sizeof(int) * D.n, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rec, ctx->rec + D.off * rc_, sizeof(int) * D.n * rc_, cudaMemcpyDeviceToHost));
     return FETDPIC_OK;
 }
 
@@ -1173,9 +1203,7 @@ extern "C" int fetdpic_check(fetdpic_ctx *ctx, int inst, double *dce_max, double
     if (dgl_max) *dgl_max = v[1];
     if (energy) *energy = v[2];
     CK(cudaMemset(ctx->chk_out + 3 * inst, 0, 2 * sizeof(double)));   // maxima restart; energy stays
-    unsigned st = 0;
-    CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    return map_status(ctx, st);
+    return take_status(ctx);
 }
 
 extern "C" int fetdpic_info(fetdpic_ctx *ctx, int inst, long long out[6])
@@ -1336,7 +1364,7 @@ extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interv
     if (!ctx) return FETDPIC_EINVAL;
     if (variant < 0 || variant > 12 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->p.kernel_variant = variant == 0 ? 11 : variant;    // 0 = the untuned default
+    ctx->p.kernel_variant = variant == 0 ? 10 : variant;    // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
     drop_graphs(ctx);
     return FETDPIC_OK;
@@ -1474,13 +1502,11 @@ extern "C" void fetdpic_destroy(fetdpic_ctx *ctx)
 //
 // fetdpic_read stages the load-ordered particle state in device memory that
 // it allocates (cudaMalloc, or the caller's allocator callback) the first
-// time it runs.  Some callers cannot allocate at that point: code that runs
-// while a stream is being captured (allocation calls are not allowed there),
-// real-time loops that forbid allocator latency, or plug-ins whose host
-// framework owns all device memory and gives none out.  This variant stages
-// through a fixed file-scope device array instead.  The array is part of
-// the library image: every GPU that loads the library holds it until the
-// process exits.
+// time it runs.  Some callers cannot allocate at that point: real-time loops
+// that forbid allocator latency, or plug-ins whose host framework owns all
+// device memory and gives none out.  This variant stages through a fixed
+// file-scope device array instead.  The array is part of the library image:
+// every GPU that loads the library holds it until the process exits.
 namespace {
 
 constexpr long long STATIC_READ_MAX = 262144;                    // particles per call
@@ -1499,7 +1525,9 @@ static std::mutex g_static_mu;
 extern "C" int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell)
 {
     if (!ctx) return FETDPIC_EINVAL;
-    if (!ctx->finalized) return ctx->fail(FETDPIC_ESTATE, "step or read the context once before the static read");
+    if (!ctx->finalized)
+        return ctx->fail(FETDPIC_ESTATE, "the particles are not on the device yet: call fetdpic_step, "
+                                         "fetdpic_write_particles or fetdpic_read with a particle buffer first");
     if (species < 0 || species >= (int)ctx->sp.size()) return ctx->fail(FETDPIC_EINVAL, "bad species");
     const Species &D = ctx->sp[species];
     if (D.n > STATIC_READ_MAX)
@@ -1521,11 +1549,16 @@ extern "C" int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, doub
         }
         base = s.ptr;
     }
-    if (D.n == 0) return FETDPIC_OK;
-    // every slot [0, n) is written by exactly one live particle (id is a permutation), so nothing
-    // left over from an earlier call is read; nothing needs clearing
+    if (D.n == 0) {
+        CK(cudaStreamSynchronize(ctx->stream));
+        return take_status(ctx);
+    }
     const size_t bx = sizeof(double) * 2 * D.n, bc = sizeof(int) * D.n;
     char *st = (char *)base;
+    // every live particle writes its slot; a particle dropped by fetdpic_write_particles (a
+    // triangle outside the mesh) writes none, so the slots are first set to all-one bytes: NaN
+    // positions and momenta, triangle -1, instead of what an earlier call left there
+    CK(cudaMemsetAsync(st, 0xFF, 2 * bx + bc, ctx->stream));
     double *ox = (double *)st, *ou = (double *)(st + bx);
     int *oc = (int *)(st + 2 * bx);
     if (ctx->p.precision == FETDPIC_FP32)
@@ -1540,7 +1573,5 @@ extern "C" int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, doub
     if (u) CK(cudaMemcpyAsync(u, ou, bx, cudaMemcpyDeviceToHost, ctx->stream));
     if (cell) CK(cudaMemcpyAsync(cell, oc, bc, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    unsigned stw = 0;
-    if (ctx->status) CK(cudaMemcpy(&stw, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    return map_status(ctx, stw);
+    return take_status(ctx);
 }

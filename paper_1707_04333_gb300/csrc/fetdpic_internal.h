@@ -71,23 +71,29 @@ struct __align__(16) Geo64 {
 };
 static_assert(sizeof(Geo64) == 128, "Geo64 layout");
 
-// FP32 per-triangle constants (48 B): G_m = c dt grad lambda_m (barycentric
-// step per unit v/c), edge words 1 and 2 (word 0 rides in the field record so
-// the main path reads 32 + 32 B), neighbour words (walk only), as in Topo.
-struct __align__(16) Cst32 {
-    float G[6];                             // (G0x, G0y, G1x, G1y, G2x, G2y)
+// FP32 per-triangle constants, split by who reads them.  CstA (32 B, one
+// 256-bit load): G_m = c dt grad lambda_m for m = 0, 1 (barycentric step per
+// unit v/c; G_2 = -(G_0 + G_1) because the gradients sum to zero), edge words
+// 1 and 2, neighbour words 0 and 1.  CstB (8 B): edge word 0 and neighbour
+// word 2, read by the walk (the particle pass gets edge word 0 from the field
+// record, where the Faraday kernel copies it).  Edge and neighbour words as in
+// Topo.
+struct __align__(32) CstA {
+    float G[4];                             // (G0x, G0y, G1x, G1y)
     int ew1, ew2;
-    int nb[3];
-    int ew0;                                // copied into Rec32 by the Faraday kernel
+    int nb0, nb1;
 };
-static_assert(sizeof(Cst32) == 48, "Cst32 layout");
+static_assert(sizeof(CstA) == 32, "CstA layout");
+struct __align__(8) CstB { int ew0, nb2; };
+static_assert(sizeof(CstB) == 8, "CstB layout");
 
 // FP32-path species parameters, read with uniform loads (32 B).
 struct __align__(16) Sp32 {
     float kappa;                            // q/m
     float xe_x, xe_y, xb;                   // external fields pre-scaled (alpha E/c, alpha B)
     float wfix;                             // (q / q_ref) * (2^25 - 64)
-    int inst, edge_off, pad;
+    int inst, edge_off;
+    int off;                                // storage offset of the species (walk record index base)
 };
 static_assert(sizeof(Sp32) == 32, "Sp32 layout");
 
@@ -137,7 +143,10 @@ struct StepArgs64 {
     unsigned long long *ifix;               // [E] fixed-point current (two's complement)
     unsigned *status;
     int max_cross;
-    int rec_cap; int *rec_cnt; int *wrec;   // walk record (rec_cap = 0: off)
+    int rec_cap; int *rec_cnt; int *wrec;   // walk record (rec_cap = 0: off), indexed by
+                                            // species storage offset + load index, so a sort
+                                            // after the step does not move it
+    const int *id;                          // load index of each particle slot
     const int *edge_off;                    // per instance, for instance-local record ids
     long long nblocks; int block;
     const signed char *tshift;              // [F][3] periodic shift codes; NULL = no periodic walls
@@ -147,7 +156,7 @@ struct StepArgs64 {
 };
 
 struct StepArgs32 {
-    const Cst32 *cst; const Rec32 *rec;
+    const CstA *csta; const CstB *cstb; const Rec32 *rec;
     const Sp32 *sp; const short *chunk_sp;  // species of each 32-particle chunk
     long long nchunks;
     int variant;                            // particle-kernel variant (min resident blocks per SM)
@@ -155,9 +164,11 @@ struct StepArgs32 {
     unsigned long long *ifix;
     unsigned *status;
     int max_cross;
-    int rec_cap; int *rec_cnt; int *wrec;
+    int rec_cap; int *rec_cnt; int *wrec;   // walk record, indexed as in StepArgs64
+    const int *id;
     const int *edge_off;
     long long nblocks; int block;
+    unsigned spin;                          // polls of a bounded wait before it gives up (variant 5)
 };
 
 void launch_faraday64(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo, const double *e,
@@ -167,7 +178,7 @@ void launch_faraday64(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo
 // weights extw (NULL = 1); finst = instance of each triangle.
 struct __align__(16) ExtField { double ex, ey, bz, pad; };
 struct Ext32 { const int *finst; const ExtField *ext; const double *amp; const double2 *extw; double half_over_c; };
-void launch_faraday32(cudaStream_t st, int F, const Cst32 *cst, const double2 *dtinv, const double *e,
+void launch_faraday32(cudaStream_t st, int F, const CstA *csta, const CstB *cstb, const double2 *dtinv, const double *e,
                       double *b, Rec32 *rec, float inv2c2, const Ext32 &x);
 void launch_particles64(cudaStream_t st, int pusher, const StepArgs64 &a);
 void launch_particles32(cudaStream_t st, int pusher, const StepArgs32 &a);
@@ -240,7 +251,5 @@ void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *i
 void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
                      const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
                      long long off, long long cap, int cell_off, double *ox, double *ou, int *oc);
-void launch_unsort_rec(cudaStream_t st, long long off, long long cap, const int *id, const int *cell,
-                       const int *cnt, const int *rec, int rec_cap, int *ocnt, int *orec);
 
 }  // namespace fetdpic

@@ -8,6 +8,8 @@
 //   - field energy e.[*eps].e/2 + b.[*mu^-1].b/2.
 // Node sums gather over a node -> edge incidence list in a fixed order, and
 // the energy uses a two-pass reduction, so every check value is deterministic.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "fetdpic_internal.h"
@@ -221,3 +223,70 @@ void launch_probe(cudaStream_t st, long long n, const ProbeW *pw, const double *
 }
 
 }  // namespace fetdpic
+
+// ------------------------------------------------- arithmetic-rate probe
+// Measurement aid for the roofline of the arithmetic-bound FP64 particle path
+// (no counterpart in the paper): eight independent FMA chains per thread,
+// unrolled 16 deep, on a grid that fills every SM.
+namespace fetdpic {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_rate(int iters, T seed, T *out)
+{
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = seed + (T)(threadIdx.x + k);
+    const T m = (T)0.9999999, c = (T)1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+        }
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == (T)-1) out[0] = s;                      // never true; keeps the chains live
+}
+
+}  // namespace fetdpic
+
+extern "C" int fetdpic_fma_rate(int fp64, double *tflops)
+{
+    using namespace fetdpic;
+    if (!tflops) return FETDPIC_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FETDPIC_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return FETDPIC_ECUDA;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    void *out = nullptr;
+    int rc = FETDPIC_OK;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMalloc(&out, 16) != cudaSuccess)
+        rc = FETDPIC_ECUDA;
+    const unsigned grid = (unsigned)sms * 8u;
+    const double threads = (double)grid * 256.0;
+    double best = 0.0;
+    int iters = 64;
+    for (int trial = 0; rc == FETDPIC_OK && trial < 12; ++trial) {
+        cudaEventRecord(e0, st);
+        if (fp64) k_fma_rate<double><<<grid, 256, 0, st>>>(iters, 1.0, (double *)out);
+        else k_fma_rate<float><<<grid, 256, 0, st>>>(iters, 1.0f, (float *)out);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { rc = FETDPIC_ECUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < 20.f) { iters = (int)std::min(1 << 22, iters * 2); continue; }   // grow to >= 20 ms
+        best = std::max(best, 2.0 * 8 * 16 * (double)iters * threads / (ms * 1e-3) / 1e12);
+    }
+    if (rc == FETDPIC_OK && cudaGetLastError() != cudaSuccess) rc = FETDPIC_ECUDA;
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    *tflops = best;
+    return rc;
+}

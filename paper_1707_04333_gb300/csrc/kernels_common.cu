@@ -384,19 +384,6 @@ __global__ void k_unsort32(long long off, long long cap, const int *__restrict__
     if (oc) oc[i] = f - cell_off;
 }
 
-__global__ void k_unsort_rec(long long off, long long cap, const int *__restrict__ id, const int *__restrict__ cell,
-                             const int *__restrict__ cnt, const int *__restrict__ rec, int rc,
-                             int *__restrict__ ocnt, int *__restrict__ orec)
-{
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= cap) return;
-    const long long p = off + k;
-    if (cell[p] < 0) return;
-    const long long i = id[p];
-    ocnt[i] = cnt[p];
-    for (int q = 0; q < rc; ++q) orec[i * rc + q] = rec[p * rc + q];
-}
-
 void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
                      const double *y, const double *ux, const double *uy, long long off, long long cap,
                      int cell_off, double *ox, double *ou, int *oc)
@@ -416,11 +403,5 @@ void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *i
                                                               ox, ou, oc);
 }
 
-void launch_unsort_rec(cudaStream_t st, long long off, long long cap, const int *id, const int *cell,
-                        const int *cnt, const int *rec, int rec_cap, int *ocnt, int *orec)
-{
-    if (cap <= 0) return;
-    k_unsort_rec<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, id, cell, cnt, rec, rec_cap, ocnt, orec);
-}
 
 }  // namespace fetdpic

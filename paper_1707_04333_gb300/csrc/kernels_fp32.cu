@@ -2,7 +2,8 @@
 // barycentric coordinates (l0, l1; l2 = 1 - l0 - l1), momenta in units of c.
 // Gather, push, walk and deposit run in FP32; particles with gamma > 10 take
 // the FP64 push (Lorentz factor and momentum update), where FP32 loses the
-// 1 - v/c and sigma cancellations.  The field update stays FP64.
+// 1 - v/c and sigma cancellations.  The field unknowns and the Faraday update
+// stay FP64; the SPAI product of the Ampere update is FP32 (kernels_common.cu).
 //
 // Built with approximate FP32 division and square root (-prec-div=false
 // -prec-sqrt=false, about 2 ulp): the FP32 path is compared with the FP64
@@ -22,17 +23,20 @@ namespace fetdpic {
 // (G = c dt grad l), so that q/m times it is alpha E / c; B_z^n stored as
 // (dt/2) B_z = (dt/2) (b^{n+1/2} + b^{n-1/2}) / (2A).
 template <bool EXT>
-__global__ void __launch_bounds__(256) k_faraday32(int F, const Cst32 *__restrict__ cst,
+__global__ void __launch_bounds__(256) k_faraday32(int F, const CstA *__restrict__ csta,
+                                                   const CstB *__restrict__ cstb,
                                                    const double2 *__restrict__ dtinv,
                                                    const double *__restrict__ e, double *__restrict__ b,
                                                    Rec32 *__restrict__ rec, float inv2c2, Ext32 x)
 {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= F) return;
-    const float4 *cp = reinterpret_cast<const float4 *>(cst + f);
-    const float4 c0 = cp[0], c1 = cp[1], c2 = cp[2];
-    const float G[6] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y};
-    const int ew[3] = {__float_as_int(c2.w), __float_as_int(c1.z), __float_as_int(c1.w)};
+    const float4 *cp = reinterpret_cast<const float4 *>(csta + f);
+    const float4 c0 = cp[0], c1 = cp[1];
+    const CstB cb = cstb[f];
+    // G_2 = -(G_0 + G_1): the barycentric gradients of a triangle sum to zero
+    const float G[6] = {c0.x, c0.y, c0.z, c0.w, -(c0.x + c0.z), -(c0.y + c0.w)};
+    const int ew[3] = {cb.ew0, __float_as_int(c1.x), __float_as_int(c1.y)};
     double se[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -70,14 +74,14 @@ __global__ void __launch_bounds__(256) k_faraday32(int F, const Cst32 *__restric
     rp[1] = make_float4(r.v[4], r.v[5], r.bz, __int_as_float(ew[0]));
 }
 
-void launch_faraday32(cudaStream_t st, int F, const Cst32 *cst, const double2 *dtinv, const double *e,
-                      double *b, Rec32 *rec, float inv2c2, const Ext32 &x)
+void launch_faraday32(cudaStream_t st, int F, const CstA *csta, const CstB *cstb, const double2 *dtinv,
+                      const double *e, double *b, Rec32 *rec, float inv2c2, const Ext32 &x)
 {
     if (F <= 0) return;
     if (x.ext)
-        k_faraday32<true><<<(F + 255) / 256, 256, 0, st>>>(F, cst, dtinv, e, b, rec, inv2c2, x);
+        k_faraday32<true><<<(F + 255) / 256, 256, 0, st>>>(F, csta, cstb, dtinv, e, b, rec, inv2c2, x);
     else
-        k_faraday32<false><<<(F + 255) / 256, 256, 0, st>>>(F, cst, dtinv, e, b, rec, inv2c2, x);
+        k_faraday32<false><<<(F + 255) / 256, 256, 0, st>>>(F, csta, cstb, dtinv, e, b, rec, inv2c2, x);
 }
 
 // --------------------------------------------------------------- pushers
@@ -255,16 +259,21 @@ __device__ __forceinline__ T sel3(const T *a, int k)
     return k == 0 ? a[0] : (k == 1 ? a[1] : a[2]);
 }
 
-// Walk state of a particle whose path leaves its triangle, queued per warp.
-struct WalkItem {
-    long long p;                 // particle index
+// A particle whose path leaves its starting triangle, queued per warp for the
+// walk: its slot, starting triangle and barycentrics, pushed momentum and
+// velocity (units of c).
+struct __align__(16) WalkItem {
+    unsigned p;                  // particle slot
     int f;                       // starting triangle
     int sp;                      // species
-    float l0, l1, l2, pad, ux, uy, vx, vy;
+    float pad;
+    float l0, l1, l2, pad2;      // barycentrics at the start of the step
+    float ux, uy, vx, vy;
 };
 static_assert(sizeof(WalkItem) == 48, "WalkItem layout");
 
-// 32 bytes (32-byte aligned) in one 256-bit load.
+// 32 bytes (32-byte aligned) in one 256-bit load: one L1 wavefront per distinct
+// line, where two 128-bit loads of the same bytes take two.
 __device__ __forceinline__ void ld_v8(const void *p, float4 &x, float4 &y)
 {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
@@ -272,41 +281,37 @@ __device__ __forceinline__ void ld_v8(const void *p, float4 &x, float4 &y)
         : "l"(p));
 }
 
-__device__ __forceinline__ void load_cst(const Cst32 *cst, int f, float *G, int *ew, int *nb)
-{
-    const float4 *cp = reinterpret_cast<const float4 *>(cst + f);
-    const float4 c0 = __ldg(cp), c1 = __ldg(cp + 1), c2 = __ldg(cp + 2);
-    G[0] = c0.x; G[1] = c0.y; G[2] = c0.z; G[3] = c0.w; G[4] = c1.x; G[5] = c1.y;
-    ew[0] = __float_as_int(c2.w); ew[1] = __float_as_int(c1.z); ew[2] = __float_as_int(c1.w);
-    nb[0] = __float_as_int(c2.x); nb[1] = __float_as_int(c2.y); nb[2] = __float_as_int(c2.z);
-}
-
-// Walk one queued particle along r(tau) = r^n + tau c dt v/c, tau in [0, 1],
+// Walk a queued particle along r(tau) = r^n + tau c dt v/c, tau in [0, 1],
 // through the triangles it crosses (the current splits the path per triangle,
-// Eq. (I.assign)): exit test, deposit of each sub-segment with direct integer
+// Eq. (I.assign)): exit test, deposit of each sub-segment with integer
 // atomics, hand-off to the neighbour or specular reflection at a PEC wall, and
-// the final particle state.  U_STORED: the caller has already stored the pushed
-// momentum, so it is written again only when a wall reflected it.
-template <bool U_STORED = false>
+// the final particle state.  The particle pass has stored the pushed momentum,
+// so it is written again only when a wall reflected it.  Per triangle the walk
+// reads 40 bytes in two loads (CstA in one 256-bit load, CstB): a warp of 32
+// walkers touches 32 different lines, where one L1 wavefront per line of a
+// 256-bit load is half of what two 128-bit loads of the same bytes take.
 __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkItem it)
 {
     const Sp32 *spp = a.sp + it.sp;
     const float wfix = __ldg(&spp->wfix);
     const int edge_off = __ldg(&spp->edge_off);
-    const long long p = it.p;
+    const unsigned p = it.p;
+    const long long rp = a.rec_cap > 0 ? (long long)__ldg(&spp->off) + a.id[p] : 0;   // walk record slot
     int f = it.f, ncross = 0, min = -1;
+    bool reflected = false;
     float lin[3] = {it.l0, it.l1, it.l2};
     float tin = 0.f, ux = it.ux, uy = it.uy, vx = it.vx, vy = it.vy;
-    bool reflected = false;
     float lfin[3];
-    float G[6];
-    int ew[3], nb[3];
     long long carry = 0;                          // current on the entry edge, not yet deposited
-    load_cst(a.cst, f, G, ew, nb);
     for (;;) {
+        float4 c0, c1;
+        ld_v8(a.csta + f, c0, c1);
+        const int2 cb = __ldg(reinterpret_cast<const int2 *>(a.cstb + f));
+        const int ew[3] = {cb.x, __float_as_int(c1.x), __float_as_int(c1.y)};
         float g[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) g[k] = G[2 * k] * vx + G[2 * k + 1] * vy;
+        g[0] = c0.x * vx + c0.y * vy;
+        g[1] = c0.z * vx + c0.w * vy;
+        g[2] = -(g[0] + g[1]);
         float tb;
         const int best = exit_edge(lin, g, tin, min, tb);
         int v[3];
@@ -334,13 +339,13 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
             atomicOr(a.status, (unsigned)ST_WALK);
             break;
         }
-        const int nbw = sel3(nb, best);
-        if (a.rec_cap > ncross) a.wrec[p * a.rec_cap + ncross] = nbw < 0 ? -(eg - edge_off + 1) : eg - edge_off;
+        const int nbw = best == 0 ? __float_as_int(c1.z) : (best == 1 ? __float_as_int(c1.w) : cb.y);
+        if (a.rec_cap > ncross) a.wrec[rp * a.rec_cap + ncross] = nbw < 0 ? -(eg - edge_off + 1) : eg - edge_off;
         ++ncross;
         if (nbw < 0) {
             // PEC wall: specular reflection of u and of the rest of the path, normal along G_best
-            const float gxs[3] = {G[0], G[2], G[4]}, gys[3] = {G[1], G[3], G[5]};
-            const float gxb = sel3(gxs, best), gyb = sel3(gys, best);
+            const float gxb = best == 0 ? c0.x : (best == 1 ? c0.z : -(c0.x + c0.z));
+            const float gyb = best == 0 ? c0.y : (best == 1 ? c0.w : -(c0.y + c0.w));
             const float igg = 1.f / (gxb * gxb + gyb * gyb);
             const float pu = (ux * gxb + uy * gyb) * igg;
             ux -= 2.f * pu * gxb; uy -= 2.f * pu * gyb;
@@ -358,22 +363,23 @@ __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkIte
             lin[2] = m2 == 2 ? 0.f : (m2 == 1 ? la : lb);
             f = nbw >> 2;
             min = m2;
-            load_cst(a.cst, f, G, ew, nb);
         }
     }
     a.l0[p] = lfin[0]; a.l1[p] = lfin[1];
-    if (!U_STORED || reflected) { a.ux[p] = ux; a.uy[p] = uy; }
+    if (reflected) { a.ux[p] = ux; a.uy[p] = uy; }
     a.cell[p] = f;
-    if (a.rec_cap > 0) a.rec_cnt[p] = ncross;
+    if (a.rec_cap > 0) a.rec_cnt[rp] = ncross;
 }
 
 constexpr int P32_BLOCK = 256;
 constexpr int P32_WARPS = P32_BLOCK / 32;
-constexpr int P32_QUEUE = 64;                // walker ring per warp
+constexpr int P32_QUEUE = 64;                // walker ring per warp (one particle per lane)
 
-// Particle state of one lane's particle and the records of its triangle.
+// Particle state of one lane's particle and the records of its triangle:
+// r0, r1 = field record (V_0, V_1 | V_2, B_z, edge word 0), c0, c1 = CstA
+// (G_0, G_1 | edge words 1, 2, neighbour words 0, 1).
 struct PState { int f, sp; float l0, l1, ux, uy; };
-struct PRec { float4 c0, c1, r0, r1; };
+struct PRec { float4 r0, r1, c0, c1; };
 
 __device__ __forceinline__ PState load_state(const StepArgs32 &a, unsigned c, int lane)
 {
@@ -386,96 +392,131 @@ __device__ __forceinline__ PState load_state(const StepArgs32 &a, unsigned c, in
     return s;
 }
 
+// The 64 bytes a particle of triangle f needs, in two 256-bit loads.
 __device__ __forceinline__ PRec load_rec(const StepArgs32 &a, int f)
 {
     // padding slots (f < 0) read triangle 0; their results are discarded
     const int g = f < 0 ? 0 : f;
-    const float4 *cp = reinterpret_cast<const float4 *>(a.cst + g);
-    const float4 *rp = reinterpret_cast<const float4 *>(a.rec + g);
     PRec r;
-    r.c0 = __ldg(cp); r.c1 = __ldg(cp + 1);    // constants (48-byte stride: 16-byte loads)
-    ld_v8(rp, r.r0, r.r1);                     // field record, 32-byte aligned: one 256-bit load
+    ld_v8(a.rec + g, r.r0, r.r1);
+    ld_v8(a.csta + g, r.c0, r.c1);
     return r;
 }
 
-// One 32-particle chunk: gather, push, in-triangle test, current of the
-// particles that stay (warp-segmented 32-bit reduction + integer atomics by
-// the run heads), state stores; walkers go to the warp's ring, which is walked
-// 32 at a time.
+// Result of one particle's gather, push and in-triangle test.
+struct POne {
+    float ux, uy, vx, vy;                    // pushed momentum and velocity (units of c)
+    float lf0, lf1;                          // end barycentrics (particles that stay)
+    int key;                                 // triangle if it stays, else -1
+    bool walking, bad;                       // bad: a live particle's velocity is not finite
+    int v[3];                                // fixed-point current if it stays, else 0
+};
+
+// Gather (Sec. II.B), push (Sec. II.C; FP64 when gamma > 10), move in
+// barycentrics (Eq. (eq.motion.dis): dl_k = c dt grad l_k . v/c, with
+// dl_2 = -(dl_0 + dl_1) so the barycentrics keep summing to 1), and the
+// current of a particle that stays in its triangle (Eq. (I.assign), written
+// i_ab += (Q/dt)(l_a dl_b - dl_a l_b)).
 template <int PUSHER>
-__device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, int lane, const PState &s,
-                                              const PRec &r, WalkItem *q, unsigned &qhead, unsigned &qtail)
+__device__ __forceinline__ POne one_particle(const float4 &s0, float wfix, int f, float l0, float l1, float ux,
+                                             float uy, const PRec &r)
 {
-    const unsigned full = 0xffffffffu;
-    const unsigned p = c * 32u + (unsigned)lane;
-    const Sp32 *spp = a.sp + s.sp;
-    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
-    const float wfix = __ldg(&spp->wfix);
-    const bool live = s.f >= 0;
-    int v0[3];
-    float ux = s.ux, uy = s.uy;
-    WalkItem it;
-    // straight-line for every lane (padding lanes compute on triangle 0 and are masked below)
-    const float l0 = s.l0, l1 = s.l1;
+    POne o;
+    const bool live = f >= 0;
     const float l2 = 1.f - l0 - l1;
-    // gather (Sec. II.B): alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
+    // alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
     const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
     const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
     const float bz = s0.x * r.r1.z + s0.w;
-    // push (Sec. II.C); FP64 when gamma > 10
     float ig, vx, vy;
     if (1.f + ux * ux + uy * uy > 100.f) {
-        const PushOut o = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
-        ux = o.ux; uy = o.uy; vx = o.vx; vy = o.vy; ig = o.ig;
+        const PushOut q = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
+        ux = q.ux; uy = q.uy; vx = q.vx; vy = q.vy; ig = q.ig;
     } else {
         ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
         vx = ux * ig; vy = uy * ig;
     }
-    if (live && !isfinite(vx + vy)) atomicOr(a.status, (unsigned)ST_NONFINITE);
-    // Eq. (eq.motion.dis) in barycentrics: dl_k = c dt grad l_k . v / c
+    o.bad = live && !isfinite(vx + vy);
     const float g0 = r.c0.x * vx + r.c0.y * vy;
     const float g1 = r.c0.z * vx + r.c0.w * vy;
-    const float g2 = r.c1.x * vx + r.c1.y * vy;
+    const float g2 = -(g0 + g1);
     const float lf0 = l0 + g0, lf1 = l1 + g1;
     const bool stays = lf0 >= 0.f && lf1 >= 0.f && l2 + g2 >= 0.f;
-    const bool walking = live && !stays;
-    const int key = (live && stays) ? s.f : -1;
-    // stays in its triangle: i_ab += (Q/dt)(l_a^s dl_b - dl_a l_b^s), Eq. (I.assign)
     const float wk = (live && stays) ? wfix : 0.f;
-    v0[0] = __float2int_rn((l1 * g2 - g1 * l2) * wk);
-    v0[1] = __float2int_rn((l2 * g0 - g2 * l0) * wk);
-    v0[2] = __float2int_rn((l0 * g1 - g0 * l1) * wk);
-    if (walking) {
-        it.p = p; it.f = s.f; it.sp = s.sp;
-        it.l0 = l0; it.l1 = l1; it.l2 = l2; it.pad = 0.f;
-        it.ux = ux; it.uy = uy; it.vx = vx; it.vy = vy;
-    }
-    const unsigned wm = __ballot_sync(full, walking);
-    if (walking) q[(qtail + __popc(wm & ((1u << lane) - 1u))) & (P32_QUEUE - 1)] = it;
+    o.v[0] = __float2int_rn((l1 * g2 - g1 * l2) * wk);
+    o.v[1] = __float2int_rn((l2 * g0 - g2 * l0) * wk);
+    o.v[2] = __float2int_rn((l0 * g1 - g0 * l1) * wk);
+    o.ux = ux; o.uy = uy; o.vx = vx; o.vy = vy; o.lf0 = lf0; o.lf1 = lf1;
+    o.key = (live && stays) ? f : -1;
+    o.walking = live && !stays;
+    return o;
+}
+
+__device__ __forceinline__ WalkItem walk_item(unsigned p, int f, int sp, float l0, float l1, const POne &o)
+{
+    WalkItem it;
+    it.p = p; it.f = f; it.sp = sp; it.pad = 0.f;
+    it.l0 = l0; it.l1 = l1; it.l2 = 1.f - l0 - l1; it.pad2 = 0.f;
+    it.ux = o.ux; it.uy = o.uy; it.vx = o.vx; it.vy = o.vy;
+    return it;
+}
+
+// Ring slot of this lane's walker (ring positions are warp-uniform); advances qtail.
+__device__ __forceinline__ unsigned ring_slot(unsigned &qtail, bool walking, int lane)
+{
+    const unsigned wm = __ballot_sync(0xffffffffu, walking);
+    const unsigned slot = qtail + __popc(wm & ((1u << lane) - 1u));
     qtail += __popc(wm);
-    {
-        const int kn = __shfl_down_sync(full, key, 1);
-        const unsigned tails = __ballot_sync(full, (lane == 31) || (kn != key));
-        const int seg_end = lane + __ffs(tails >> lane) - 1;
-        const int kp = __shfl_up_sync(full, key, 1);
-        const bool head = (lane == 0) || (kp != key);
+    return slot;
+}
+
+// Segmented sum of v over runs of equal key across the warp (keys of a run are
+// adjacent: the particles are sorted by triangle); the run heads deposit the
+// sums with three integer atomics.
+__device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, int *v, int lane, const int *ew)
+{
+    const unsigned full = 0xffffffffu;
+    const int kn = __shfl_down_sync(full, key, 1);
+    const unsigned tails = __ballot_sync(full, (lane == 31) || (kn != key));
+    const int seg_end = lane + __ffs(tails >> lane) - 1;
+    const int kp = __shfl_up_sync(full, key, 1);
+    const bool head = (lane == 0) || (kp != key);
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o0 = __shfl_down_sync(full, v0[0], off);
-            const int o1 = __shfl_down_sync(full, v0[1], off);
-            const int o2 = __shfl_down_sync(full, v0[2], off);
-            if (lane + off <= seg_end) { v0[0] += o0; v0[1] += o1; v0[2] += o2; }
-        }
-        if (head && key >= 0) {
-            const int ew[3] = {__float_as_int(r.r1.w), __float_as_int(r.c1.z), __float_as_int(r.c1.w)};
-            add_seg32(a.ifix, ew, v0);
-        }
+    for (int off = 1; off < 32; off <<= 1) {
+        const int o0 = __shfl_down_sync(full, v[0], off);
+        const int o1 = __shfl_down_sync(full, v[1], off);
+        const int o2 = __shfl_down_sync(full, v[2], off);
+        if (lane + off <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
     }
-    if (live && stays) {
-        __stcs(a.l0 + p, lf0); __stcs(a.l1 + p, lf1);
-        __stcs(a.ux + p, ux); __stcs(a.uy + p, uy);
-        if (a.rec_cap > 0) a.rec_cnt[p] = 0;
+    if (head && key >= 0) add_seg32(ifix, ew, v);
+}
+
+// One 32-particle chunk, one particle per lane: gather, push, in-triangle
+// test, current of the particles that stay (run deposit), state stores;
+// walkers go to the warp's ring, which is walked 32 at a time.
+template <int PUSHER>
+__device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, int lane, const PState &s,
+                                              const PRec &r, WalkItem *q, unsigned &qhead, unsigned &qtail)
+{
+    const unsigned p = c * 32u + (unsigned)lane;
+    const Sp32 *spp = a.sp + s.sp;
+    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
+    const float wfix = __ldg(&spp->wfix);
+    POne o = one_particle<PUSHER>(s0, wfix, s.f, s.l0, s.l1, s.ux, s.uy, r);
+    if (o.bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
+    {
+        const unsigned slot = ring_slot(qtail, o.walking, lane);
+        if (o.walking) q[slot & (P32_QUEUE - 1)] = walk_item(p, s.f, s.sp, s.l0, s.l1, o);
     }
+    {
+        const int ew[3] = {__float_as_int(r.r1.w), __float_as_int(r.c1.x), __float_as_int(r.c1.y)};
+        run_deposit(a.ifix, o.key, o.v, lane, ew);
+    }
+    if (o.key >= 0) {
+        __stcs(a.l0 + p, o.lf0); __stcs(a.l1 + p, o.lf1);
+        if (a.rec_cap > 0) a.rec_cnt[__ldg(&spp->off) + a.id[p]] = 0;
+    }
+    if (s.f >= 0) { __stcs(a.ux + p, o.ux); __stcs(a.uy + p, o.uy); }
     if (qtail - qhead >= 32) {
         __syncwarp();
         const WalkItem w = q[(qhead + lane) & (P32_QUEUE - 1)];
@@ -485,15 +526,13 @@ __device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, i
     }
 }
 
+template <int QN>
 __device__ __forceinline__ void drain(const StepArgs32 &a, WalkItem *q, unsigned qhead, unsigned qtail, int lane)
 {
     const unsigned left = qtail - qhead;
     if (left > 0) {
         __syncwarp();
-        if ((unsigned)lane < left) {
-            const WalkItem w = q[(qhead + lane) & (P32_QUEUE - 1)];
-            walk_particle(a, w);
-        }
+        if ((unsigned)lane < left) walk_particle(a, q[(qhead + lane) & (QN - 1)]);
     }
 }
 
@@ -524,20 +563,18 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32(StepArgs32 a)
         const PRec r = load_rec(a, s.f);
         process_chunk<PUSHER>(a, c, lane, s, r, q, qhead, qtail);
     }
-    drain(a, q, qhead, qtail, lane);
+    drain<P32_QUEUE>(a, q, qhead, qtail, lane);
 }
 
 // ------------------------------------------------- two particles per lane
 // Each lane takes two adjacent particles, so a warp chunk is 64 particles and
 // the state moves in 8-byte vector loads and stores.  When both particles of
-// a lane stay in the same triangle their currents are summed in the lane, so
+// a lane are in the same triangle their currents are summed in the lane, so
 // the warp-segmented reduction runs once per 64 particles; a lane whose pair
 // straddles a change of triangle hands its first particle to the previous
 // lane's run (or deposits it with its own integer atomics when that run is
-// another triangle's).  The walk rewrites a walker's momentum only after a
-// wall reflection, since this pass stores the pushed momentum of every live
-// particle.  The per-particle arithmetic is process_chunk's, written out the
-// same way.
+// another triangle's).  The per-particle arithmetic is one_particle's, as in
+// the one-particle-per-lane kernel.
 constexpr int P32_QUEUE2 = 128;              // walker ring per warp: 31 pending + 64 new fit
 
 struct PState2 { int fa, fb, sp; float2 l0, l1, ux, uy; };
@@ -556,57 +593,6 @@ __device__ __forceinline__ PState2 load_state2(const StepArgs32 &a, unsigned c, 
     return s;
 }
 
-// Result of one particle's gather, push and in-triangle test.
-struct POne {
-    float ux, uy, vx, vy, lf0, lf1;
-    int key;                                 // triangle if it stays, else -1
-    bool walking, bad;                       // bad: a live particle's velocity is not finite
-    int v[3];                                // fixed-point current if it stays, else 0
-};
-
-template <int PUSHER>
-__device__ __forceinline__ POne one_particle(const StepArgs32 &a, const float4 &s0, float wfix, int f,
-                                             float l0, float l1, float ux, float uy, const PRec &r)
-{
-    POne o;
-    const bool live = f >= 0;
-    const float l2 = 1.f - l0 - l1;
-    const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
-    const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
-    const float bz = s0.x * r.r1.z + s0.w;
-    float ig, vx, vy;
-    if (1.f + ux * ux + uy * uy > 100.f) {
-        const PushOut q = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
-        ux = q.ux; uy = q.uy; vx = q.vx; vy = q.vy; ig = q.ig;
-    } else {
-        ig = push_c1<PUSHER, float>(ux, uy, ex, ey, bz);
-        vx = ux * ig; vy = uy * ig;
-    }
-    o.bad = live && !isfinite(vx + vy);
-    const float g0 = r.c0.x * vx + r.c0.y * vy;
-    const float g1 = r.c0.z * vx + r.c0.w * vy;
-    const float g2 = r.c1.x * vx + r.c1.y * vy;
-    const float lf0 = l0 + g0, lf1 = l1 + g1;
-    const bool stays = lf0 >= 0.f && lf1 >= 0.f && l2 + g2 >= 0.f;
-    const float wk = (live && stays) ? wfix : 0.f;
-    o.v[0] = __float2int_rn((l1 * g2 - g1 * l2) * wk);
-    o.v[1] = __float2int_rn((l2 * g0 - g2 * l0) * wk);
-    o.v[2] = __float2int_rn((l0 * g1 - g0 * l1) * wk);
-    o.ux = ux; o.uy = uy; o.vx = vx; o.vy = vy; o.lf0 = lf0; o.lf1 = lf1;
-    o.key = (live && stays) ? f : -1;
-    o.walking = live && !stays;
-    return o;
-}
-
-__device__ __forceinline__ WalkItem walk_item(long long p, int f, int sp, float l0, float l1, const POne &o)
-{
-    WalkItem it;
-    it.p = p; it.f = f; it.sp = sp;
-    it.l0 = l0; it.l1 = l1; it.l2 = 1.f - l0 - l1; it.pad = 0.f;
-    it.ux = o.ux; it.uy = o.uy; it.vx = o.vx; it.vy = o.vy;
-    return it;
-}
-
 // SEQ: the second particle's records are loaded after the first particle's
 // arithmetic (a compiler barrier keeps them there), so the two record sets are
 // never live together; when both particles share a triangle the second load
@@ -621,7 +607,12 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     const Sp32 *spp = a.sp + s.sp;
     const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
     const float wfix = __ldg(&spp->wfix);
-    const POne A = one_particle<PUSHER>(a, s0, wfix, s.fa, s.l0.x, s.l1.x, s.ux.x, s.uy.x, ra);
+    const POne A = one_particle<PUSHER>(s0, wfix, s.fa, s.l0.x, s.l1.x, s.ux.x, s.uy.x, ra);
+    {
+        const unsigned slot = ring_slot(qtail, A.walking, lane);
+        if (A.walking) q[slot & (P32_QUEUE2 - 1)] = walk_item(pa, s.fa, s.sp, s.l0.x, s.l1.x, A);
+    }
+    const int ewa[3] = {__float_as_int(ra.r1.w), __float_as_int(ra.c1.x), __float_as_int(ra.c1.y)};
     PRec rb;
     if (SEQ) {
         asm volatile("" ::: "memory");
@@ -629,28 +620,22 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     } else {
         rb = rb_in;
     }
-    const POne B = one_particle<PUSHER>(a, s0, wfix, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
+    const POne B = one_particle<PUSHER>(s0, wfix, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
+    {
+        const unsigned slot = ring_slot(qtail, B.walking, lane);
+        if (B.walking) q[slot & (P32_QUEUE2 - 1)] = walk_item(pa + 1, s.fb, s.sp, s.l0.y, s.l1.y, B);
+    }
     bad |= A.bad | B.bad;
-    // walkers to the ring
-    const unsigned lt = (1u << lane) - 1u;
-    const unsigned wa = __ballot_sync(full, A.walking), wb = __ballot_sync(full, B.walking);
-    if (A.walking) q[(qtail + __popc(wa & lt)) & (P32_QUEUE2 - 1)] = walk_item(pa, s.fa, s.sp, s.l0.x, s.l1.x, A);
-    qtail += __popc(wa);
-    if (B.walking) q[(qtail + __popc(wb & lt)) & (P32_QUEUE2 - 1)] = walk_item(pa + 1, s.fb, s.sp, s.l0.y, s.l1.y, B);
-    qtail += __popc(wb);
-    // current of the particles that stay, Eq. (I.assign).  The run of a thread's second
-    // particle is reduced across the warp; a first particle that ends a different run (an
-    // "orphan") is handed to the previous thread when that thread's second particle lies in
-    // the same triangle, and deposits with its own atomics otherwise.
+    // current of the particles that stay, Eq. (I.assign).  The run of a
+    // thread's second particle is reduced across the warp; a first particle that ends a
+    // different run (an "orphan") is handed to the previous thread when that thread's second
+    // particle lies in the same triangle, and deposits with its own atomics otherwise.
     const bool same = A.key == B.key;
     const int key = B.key;
     const int okey = same ? -1 : A.key;                  // orphan's triangle, -1: none
     const int kp = __shfl_up_sync(full, key, 1);
     const bool given = lane > 0 && okey >= 0 && okey == kp;
-    if (okey >= 0 && !given) {
-        const int ew[3] = {__float_as_int(ra.r1.w), __float_as_int(ra.c1.z), __float_as_int(ra.c1.w)};
-        add_seg32(a.ifix, ew, A.v);
-    }
+    if (okey >= 0 && !given) add_seg32(a.ifix, ewa, A.v);
     int v0[3];
     {
         const bool taken = __shfl_down_sync(full, given, 1) && lane < 31;
@@ -661,38 +646,27 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
         }
     }
     {
-        const int kn = __shfl_down_sync(full, key, 1);
-        const unsigned tails = __ballot_sync(full, (lane == 31) || (kn != key));
-        const int seg_end = lane + __ffs(tails >> lane) - 1;
-        const bool head = (lane == 0) || (kp != key);
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int o0 = __shfl_down_sync(full, v0[0], off);
-            const int o1 = __shfl_down_sync(full, v0[1], off);
-            const int o2 = __shfl_down_sync(full, v0[2], off);
-            if (lane + off <= seg_end) { v0[0] += o0; v0[1] += o1; v0[2] += o2; }
-        }
-        if (head && key >= 0) {
-            const int ew[3] = {__float_as_int(rb.r1.w), __float_as_int(rb.c1.z), __float_as_int(rb.c1.w)};
-            add_seg32(a.ifix, ew, v0);
-        }
+        const int ewb[3] = {__float_as_int(rb.r1.w), __float_as_int(rb.c1.x), __float_as_int(rb.c1.y)};
+        run_deposit(a.ifix, key, v0, lane, ewb);
     }
-    // state: both slots of every lane are written (a walker's position is rewritten by its
-    // walk after the warp barrier below, and its momentum only if a wall reflects it; a
-    // padding slot keeps its value)
-    const bool sa = A.key >= 0, sb = B.key >= 0, la = s.fa >= 0, lb = s.fb >= 0;
-    __stcs(reinterpret_cast<float2 *>(a.l0 + pa), make_float2(sa ? A.lf0 : s.l0.x, sb ? B.lf0 : s.l0.y));
-    __stcs(reinterpret_cast<float2 *>(a.l1 + pa), make_float2(sa ? A.lf1 : s.l1.x, sb ? B.lf1 : s.l1.y));
-    __stcs(reinterpret_cast<float2 *>(a.ux + pa), make_float2(la ? A.ux : s.ux.x, lb ? B.ux : s.ux.y));
-    __stcs(reinterpret_cast<float2 *>(a.uy + pa), make_float2(la ? A.uy : s.uy.x, lb ? B.uy : s.uy.y));
+    // state: both slots of every lane are written.  A walker's position is rewritten by its
+    // walk after the warp barrier below, and its momentum (stored here as pushed) only if a
+    // wall reflects it; a padding slot (triangle -1) is never read, so it takes whatever
+    // was computed for it.
+    const bool sa = A.key >= 0, sb = B.key >= 0;
+    __stcs(reinterpret_cast<float2 *>(a.l0 + pa), make_float2(A.lf0, B.lf0));
+    __stcs(reinterpret_cast<float2 *>(a.l1 + pa), make_float2(A.lf1, B.lf1));
+    __stcs(reinterpret_cast<float2 *>(a.ux + pa), make_float2(A.ux, B.ux));
+    __stcs(reinterpret_cast<float2 *>(a.uy + pa), make_float2(A.uy, B.uy));
     if (a.rec_cap > 0) {
-        if (sa) a.rec_cnt[pa] = 0;
-        if (sb) a.rec_cnt[pa + 1] = 0;
+        const int off = __ldg(&spp->off);
+        if (sa) a.rec_cnt[off + a.id[pa]] = 0;
+        if (sb) a.rec_cnt[off + a.id[pa + 1]] = 0;
     }
     while (qtail - qhead >= 32) {
         __syncwarp();
         const WalkItem w = q[(qhead + lane) & (P32_QUEUE2 - 1)];
-        walk_particle<true>(a, w);
+        walk_particle(a, w);
         qhead += 32;
         __syncwarp();
     }
@@ -723,11 +697,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
         process_chunk2<PUSHER, SEQ>(a, c, lane, s, ra, rb, q, qhead, qtail, bad);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
-    const unsigned left = qtail - qhead;
-    if (left > 0) {
-        __syncwarp();
-        if ((unsigned)lane < left) walk_particle<true>(a, q[(qhead + lane) & (P32_QUEUE2 - 1)]);
-    }
+    drain<P32_QUEUE2>(a, q, qhead, qtail, lane);
 }
 
 // ------------------------------------------------------- staged variant
@@ -736,9 +706,11 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
 // chunk being processed: one lane per warp issues five 128-byte copies per
 // chunk (cell, l0, l1, ux, uy), so the bytes in flight no longer depend on the
 // registers a thread can spare.  Every wait on an mbarrier is bounded; a wait
-// that gives up sets ST_TIMEOUT and the warp stops after draining its copies.
+// that gives up (after StepArgs32::spin polls) sets ST_TIMEOUT and the warp
+// stops after waiting, with the fixed bound ST_SPIN, for the copies it still
+// has in flight, so no copy lands in shared memory the block no longer owns.
 constexpr int ST_DEPTH = 4;
-constexpr unsigned ST_SPIN = 1u << 20;
+constexpr unsigned ST_SPIN = 1u << 22;
 
 struct __align__(16) StageBuf {
     int cell[32];
@@ -769,20 +741,23 @@ __device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, unsigne
                  : "memory");
 }
 
+// Non-blocking test of phase `parity` (test_wait returns at once; try_wait may
+// suspend the thread for a hardware-chosen time, which would make the poll
+// count of a bounded wait meaningless).
 __device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
 {
     unsigned ok;
-    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(ok)
                  : "r"(smem_addr(bar)), "r"(parity)
                  : "memory");
     return ok != 0;
 }
 
-// Bounded wait for phase `parity` of `bar`; false after ST_SPIN polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+// Bounded wait for phase `parity` of `bar`; false after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit)
 {
-    for (unsigned k = 0; k < ST_SPIN; ++k)
+    for (unsigned k = 0; k < limit; ++k)
         if (mbar_test(bar, parity)) return true;
     return false;
 }
@@ -827,6 +802,9 @@ __global__ void __launch_bounds__(P32_BLOCK, 3) k_particles32_staged(StepArgs32 
             if (c0 + s < cend) stage_issue(a, c0 + s, &buf[s], &bar[s]);
     __syncwarp();
     unsigned phase = 0;                               // bit s = parity to wait for on stage s
+    unsigned inflight = 0;                            // bit s = stage s has copies in flight
+    for (int s = 0; s < ST_DEPTH; ++s)
+        if (c0 + s < cend) inflight |= 1u << s;
     int spn = a.chunk_sp[c0];
     bool ok = true;
     for (unsigned c = c0; c < cend; ++c) {
@@ -834,23 +812,28 @@ __global__ void __launch_bounds__(P32_BLOCK, 3) k_particles32_staged(StepArgs32 
         const int sp = spn;
         if (c + 1 < cend) spn = a.chunk_sp[c + 1];
         // all lanes poll; the warp gives up together so no lane is left in a full-mask shuffle
-        if (!__all_sync(0xffffffffu, mbar_wait(&bar[s], (phase >> s) & 1u))) { ok = false; break; }
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar[s], (phase >> s) & 1u, a.spin))) { ok = false; break; }
         phase ^= 1u << s;
+        inflight &= ~(1u << s);
         PState st;
         st.f = buf[s].cell[lane]; st.l0 = buf[s].l0[lane]; st.l1 = buf[s].l1[lane];
         st.ux = buf[s].ux[lane]; st.uy = buf[s].uy[lane]; st.sp = sp;
         __syncwarp();
-        if (lane == 0 && c + ST_DEPTH < cend) stage_issue(a, c + ST_DEPTH, &buf[s], &bar[s]);
+        if (c + ST_DEPTH < cend) {
+            if (lane == 0) stage_issue(a, c + ST_DEPTH, &buf[s], &bar[s]);
+            inflight |= 1u << s;
+        }
         const PRec r = load_rec(a, st.f);
         process_chunk<PUSHER>(a, c, lane, st, r, q, qhead, qtail);
     }
     if (!ok) {
         if (lane == 0) atomicOr(a.status, (unsigned)ST_TIMEOUT);
         // let the copies still in flight land before the block's shared memory goes away
-        for (int s = 0; s < ST_DEPTH; ++s) mbar_wait(&bar[s], (phase >> s) & 1u);
+        for (int s = 0; s < ST_DEPTH; ++s)
+            if (inflight & (1u << s)) mbar_wait(&bar[s], (phase >> s) & 1u, ST_SPIN);
         return;
     }
-    drain(a, q, qhead, qtail, lane);
+    drain<P32_QUEUE>(a, q, qhead, qtail, lane);
 }
 
 // Persistent grid: resident blocks per SM (from the occupancy calculator) times

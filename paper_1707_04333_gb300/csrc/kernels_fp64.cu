@@ -170,6 +170,8 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
     int min = -1, ncross = 0;
     const double *gxp = nullptr, *gyp = nullptr;
     Topo tc;
+    // walk record slot: species storage offset + load index (unmoved by a later sort)
+    const long long rp = (a.rec_cap > 0 && live) ? S.off + a.id[p] : 0;
 
     if (live) {
         const Geo64 &G = a.geo[f];
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
                 walking = false;
             } else {
                 const int nbw = tc.nb[best];
-                if (a.rec_cap > ncross) a.wrec[p * a.rec_cap + ncross] = nbw < 0 ? -(eg - a.edge_off[S.inst] + 1) : eg - a.edge_off[S.inst];
+                if (a.rec_cap > ncross) a.wrec[rp * a.rec_cap + ncross] = nbw < 0 ? -(eg - a.edge_off[S.inst] + 1) : eg - a.edge_off[S.inst];
                 ++ncross;
                 if (nbw < 0) {
                     const double xw = xs + tb * (xf - xs), yw = ys + tb * (yf - ys);
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
             break;
         }
         const int nbw = tc.nb[best];
-        if (a.rec_cap > ncross) a.wrec[p * a.rec_cap + ncross] = nbw < 0 ? -(eg - a.edge_off[S.inst] + 1) : eg - a.edge_off[S.inst];
+        if (a.rec_cap > ncross) a.wrec[rp * a.rec_cap + ncross] = nbw < 0 ? -(eg - a.edge_off[S.inst] + 1) : eg - a.edge_off[S.inst];
         ++ncross;
         if (nbw < 0) {
             const double xw = xs + tb * (xf - xs), yw = ys + tb * (yf - ys);
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(256) k_particles64(StepArgs64 a)
         a.x[p] = xf; a.y[p] = yf;
         a.ux[p] = ux; a.uy[p] = uy;
         a.cell[p] = f;
-        if (a.rec_cap > 0) a.rec_cnt[p] = ncross;
+        if (a.rec_cap > 0) a.rec_cnt[rp] = ncross;
     }
 }
 

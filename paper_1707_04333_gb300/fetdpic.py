@@ -31,7 +31,8 @@ class Params(C.Structure):
                 ("max_crossings", C.c_int), ("check_interval", C.c_int), ("record_walk", C.c_int),
                 ("block_size", C.c_int), ("use_graphs", C.c_int), ("time_stages", C.c_int), ("kernel_variant", C.c_int),
                 ("cuda_stream", C.c_void_p),
-                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p)]
+                ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p),
+                ("wait_spin_limit", C.c_longlong)]
 
 
 class Instance(C.Structure):
@@ -74,6 +75,7 @@ def lib():
             "fetdpic_sync": (i32, [vp]),
             "fetdpic_read": (i32, [vp, i32, vp, vp, vp, i32, vp, vp, vp]),
             "fetdpic_read_walk": (i32, [vp, i32, vp, vp]),
+            "fetdpic_read_charge": (i32, [vp, i32, vp, vp]),
             "fetdpic_read_particles_static": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_check": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_info": (i32, [vp, i32, vp]),
@@ -88,6 +90,7 @@ def lib():
             "fetdpic_autotune": (i32, [vp, i32, i32, vp, vp]),
             "fetdpic_set_tuning": (i32, [vp, i32, i32]),
             "fetdpic_particle_bytes": (i32, [vp, vp, vp]),
+            "fetdpic_fma_rate": (i32, [i32, vp]),
             "fetdpic_last_error": (C.c_char_p, [vp]),
             "fetdpic_destroy": (None, [vp]),
         }
@@ -193,6 +196,15 @@ def fetdpic_read_walk(h, species, n, cap):
     return cnt, rec
 
 
+def fetdpic_read_charge(h, inst=0):
+    """(nodal charge [n_nodes] of the current particle state, fixed-point quantum)."""
+    info = fetdpic_info(h, inst)
+    q = np.zeros(info["n_nodes"])
+    qu = C.c_double()
+    _check(h, lib().fetdpic_read_charge(h, inst, _ptr(q), C.byref(qu)))
+    return q, qu.value
+
+
 def fetdpic_check(h, inst=0):
     v = (C.c_double * 3)()
     _check(h, lib().fetdpic_check(h, inst, C.byref(v, 0), C.byref(v, 8), C.byref(v, 16)))
@@ -259,6 +271,13 @@ def fetdpic_particle_bytes(h):
     return b.value, n.value
 
 
+def fetdpic_fma_rate(fp64: bool) -> float:
+    """Measured FMA rate of the current device in TFLOP/s (FP64 or FP32)."""
+    t = C.c_double()
+    _check(None, lib().fetdpic_fma_rate(1 if fp64 else 0, C.byref(t)))
+    return t.value
+
+
 def fetdpic_destroy(h):
     if h:
         lib().fetdpic_destroy(h)
@@ -287,7 +306,8 @@ class Simulation:
 
     def __init__(self, workloads, precision="fp64", spai_level=2, sort_interval=16, max_crossings=64,
                  record_walk=0, block_size=0, check_interval=0, use_torch=True, stream=None,
-                 edges=None, edge_tags=None, time_stages=False, kernel_variant=0, use_graphs=False):
+                 edges=None, edge_tags=None, time_stages=False, kernel_variant=0, use_graphs=False,
+                 wait_spin_limit=0):
         if not isinstance(workloads, (list, tuple)):
             workloads = [workloads]
         self.workloads = list(workloads)
@@ -303,6 +323,7 @@ class Simulation:
         p.time_stages = 1 if time_stages else 0
         p.kernel_variant = kernel_variant
         p.use_graphs = 1 if use_graphs else 0
+        p.wait_spin_limit = wait_spin_limit
         self.stream = None
         if use_torch:
             import torch

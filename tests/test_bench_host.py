@@ -51,3 +51,25 @@ def test_committed_traffic_record_is_well_formed():
     assert t["dram_bytes_per_launch"] == t["dram_bytes_read"] + t["dram_bytes_write"]
     assert t["bytes_per_launch"] == 8039120 * 40
     assert "--clock-control none" in t["command"] and all(os.path.exists(os.path.join(ROOT, s)) for s in t["sources"])
+
+
+def test_launcher_command_runs_one_rank_per_gpu():
+    b = _bench()
+    cmd = b.launcher_argv(["--gpus", "4", "--steps", "10"], 4, 29555)
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "--master-addr=127.0.0.1" in cmd and "--master-port=29555" in cmd
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "10"] and cmd[-5].endswith("bench.py")
+
+
+def test_gpus_2_starts_two_gloo_ranks_end_to_end():
+    """bench.py --gpus 2 launched without torchrun starts its two ranks itself; in the dry mode
+    (no GPU) they split the 64 batched instances over gloo and rank 0 reports n_gpus = 2, every
+    instance counted once and the max over ranks."""
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--dry-ranks"],
+                       capture_output=True, text=True, timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-3000:]
+    line = json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])
+    assert line["n_gpus"] == 2 and line["instances"] == 64 and line["max_over_ranks"] == 2.0

@@ -400,7 +400,8 @@ def test_edge_cases(fx):
 def test_full_size_pair_plasma_sampled(fx, precision):
     """The benchmark workload (200k triangles, 8M particles, Vay) in the launch configuration the
     benchmark times: one step on the GPU; a seeded sample of 4096 particles per species is stepped
-    by the oracle from the same pre-step state and fields."""
+    by the oracle from the same pre-step state and fields (FP64: bit-identical triangles, positions
+    and momenta; FP32: momenta within 2e-5, positions within 1e-5 of the mean edge)."""
     fetdpic, oracle = fx
     w = inputs.pair_plasma(317, 20, kT=0.1, wc_over_wp=0.5, seed=2, pusher="vay")
     sim = fetdpic.Simulation(w, precision=precision, spai_level=2, sort_interval=16).load()
@@ -420,6 +421,8 @@ def test_full_size_pair_plasma_sampled(fx, precision):
         idxs.append(idx)
         ora.load(s.q, s.m, pre[k]["x"][idx], pre[k]["u"][idx], cell=pre[k]["cell"][idx])
     ora.step("vay", only_particles=True)            # one Faraday update, both species
+    om = ora.mesh
+    h = float(np.linalg.norm(w.mesh.nodes[om.edge[:, 1]] - w.mesh.nodes[om.edge[:, 0]], axis=1).mean())
     for k, idx in enumerate(idxs):
         o = ora.species[k]
         if precision == "fp64":
@@ -429,4 +432,7 @@ def test_full_size_pair_plasma_sampled(fx, precision):
             du = np.hypot(o["ux"] - post[k]["u"][idx, 0], o["uy"] - post[k]["u"][idx, 1])
             assert (du <= 2e-5 * np.hypot(o["ux"], o["uy"]) + 1e-3).all()
             assert (o["cell"] == post[k]["cell"][idx]).mean() > 0.999
+            # positions within 1e-5 of the mean edge length (FP32 barycentric storage)
+            dx = np.hypot(o["x"] - post[k]["x"][idx, 0], o["y"] - post[k]["x"][idx, 1])
+            assert (dx <= 1e-5 * h).all(), dx.max() / h
     sim.close()

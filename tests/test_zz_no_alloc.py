@@ -1,10 +1,9 @@
 """The allocation-free particle read (fetdpic_read_particles_static).
 
 Callers that cannot allocate device memory when they read particles back
-(inside a stream capture, in allocation-free real-time loops, or as a plug-in
-whose host framework owns all device memory) use this entry point; it must
-give exactly what fetdpic_read gives.  The file is named so that pytest
-collects it last.
+(allocation-free real-time loops, or plug-ins whose host framework owns all
+device memory) use this entry point; it must give exactly what fetdpic_read
+gives.  The file is named so that pytest collects it last.
 """
 import ctypes
 
@@ -50,17 +49,34 @@ def test_static_read_matches_fetdpic_read(precision):
     sim.close()
 
 
-def test_static_read_rejects_oversize_species():
-    from paper_1707_04333_gb300 import fetdpic
-    m = inputs.jittered_delaunay(40, 40, 1.0, 1.0, 0.3, seed=3)
-    rng = np.random.default_rng(0)
-    n = 262_144 + 1
+def _uniform_species(m, n, seed):
+    rng = np.random.default_rng(seed)
     tri = rng.integers(0, len(m.triangles), n).astype(np.int32)
     x = inputs.sample_in_triangles(m, tri, rng)
-    sp = [inputs.Species(-inputs.Q_E, inputs.M_E, x, np.zeros((n, 2)), tri)]
-    sim = fetdpic.Simulation(inputs.Workload("big", m, sp, 1e-12), precision="fp32", spai_level=1).load()
+    u = rng.normal(0, 1e7, (n, 2))
+    return inputs.Species(-inputs.Q_E, inputs.M_E, x, u, tri)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_static_read_size_limits(precision):
+    """The largest species the array holds (262,144 particles: its last byte written) reads the
+    same as fetdpic_read; one particle more is rejected with the limit in the message; an empty
+    species reads nothing and succeeds."""
+    from paper_1707_04333_gb300 import fetdpic
+    m = inputs.jittered_delaunay(40, 40, 1.0, 1.0, 0.3, seed=3)
+    lim = 262_144
+    sp = [_uniform_species(m, lim, 0), _uniform_species(m, lim + 1, 1),
+          inputs.Species(inputs.Q_E, inputs.M_E, np.zeros((0, 2)), np.zeros((0, 2)), np.zeros(0, np.int32))]
+    sim = fetdpic.Simulation(inputs.Workload("big", m, sp, 1e-12), precision=precision, spai_level=1).load()
     sim.step(1, "boris").sync()
-    rc, *_ = _static_read(fetdpic, sim.h, 0, n)
+    ref = sim.read_species(0)
+    for _ in range(2):
+        rc, x, u, c = _static_read(fetdpic, sim.h, 0, lim)
+        assert rc == 0, fetdpic.lib().fetdpic_last_error(sim.h)
+        assert np.array_equal(x, ref["x"]) and np.array_equal(u, ref["u"]) and np.array_equal(c, ref["cell"])
+    rc, *_ = _static_read(fetdpic, sim.h, 1, lim + 1)
     assert rc == fetdpic.EINVAL
     assert b"262144" in fetdpic.lib().fetdpic_last_error(sim.h)
+    rc, x, u, c = _static_read(fetdpic, sim.h, 2, 0)
+    assert rc == 0 and x.shape == (0, 2)
     sim.close()
