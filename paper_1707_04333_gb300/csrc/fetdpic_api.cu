@@ -83,6 +83,8 @@ struct fetdpic_ctx {
     double *ext_amp = nullptr;
     double2 *extw = nullptr;                 // NULL until a profile is set
     int *face_inst = nullptr;                // FP32: instance of each triangle
+    int *tri_c2i = nullptr;                  // [cell_off + caller index] -> stored instance-local index
+    int *tri_i2c = nullptr;                  // [stored global index] -> caller's instance-local index
     bool ext_on = false;                     // FP32: fold applied fields into the field record
     int *hist = nullptr, *hoff = nullptr, *scan_tmp = nullptr; long long hist_n = 0;
     long long *pad_adj = nullptr;
@@ -440,6 +442,8 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             ctx->tshift = ctx->alloc<signed char>(3 * (size_t)ctx->F);
             ctx->period = ctx->alloc<double2>(n_inst);
         }
+        ctx->tri_c2i = ctx->alloc<int>(ctx->F);
+        ctx->tri_i2c = ctx->alloc<int>(ctx->F);
         ctx->ext_dev = ctx->alloc<ExtField>(n_inst);
         ctx->ext_amp = ctx->alloc<double>(n_inst);
         if (P.precision == FETDPIC_FP32) ctx->face_inst = ctx->alloc<int>(ctx->F);
@@ -513,6 +517,18 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
                 for (int f = ctx->cell_off[k]; f < ctx->cell_off[k + 1]; ++f) fi[f] = k;
             rc = rc ? rc : upload(ctx, ctx->face_inst, fi.data(), fi.size());
         }
+    }
+    {
+        std::vector<int> c2i(ctx->F), i2c(ctx->F);
+        for (int k = 0; k < n_inst; ++k) {
+            const HostMesh &M = ctx->mesh[k];
+            for (int f = 0; f < M.nf; ++f) {
+                c2i[ctx->cell_off[k] + f] = M.inv[f];
+                i2c[ctx->cell_off[k] + f] = M.perm[f];
+            }
+        }
+        rc = rc ? rc : upload(ctx, ctx->tri_c2i, c2i.data(), c2i.size());
+        rc = rc ? rc : upload(ctx, ctx->tri_i2c, i2c.data(), i2c.size());
     }
     rc = rc ? rc : upload(ctx, ctx->m_soff, soff.data(), soff.size());
     rc = rc ? rc : upload(ctx, ctx->m_row, mrow.data(), mrow.size());
@@ -706,8 +722,14 @@ static int finalize(fetdpic_ctx *ctx)
         const HostMesh &M = ctx->mesh[S.inst];
         for (long long b = D.off / ctx->block; b < (D.off + D.cap) / ctx->block; ++b) blk[b] = (short)s;
         for (long long b = D.off / 32; b < (D.off + D.cap) / 32; ++b) chk[b] = (short)s;
-        for (long long k = 0; k < D.n; ++k) {
-            const long long q = D.off + k;
+        // storage in stored-triangle order from the start (a counting sort; load order in id)
+        std::vector<long long> start(M.nf + 1, 0), order(D.n);
+        for (long long k = 0; k < D.n; ++k) ++start[S.cell[k] + 1];
+        for (int f = 0; f < M.nf; ++f) start[f + 1] += start[f];
+        for (long long k = 0; k < D.n; ++k) order[start[S.cell[k]]++] = k;
+        for (long long r = 0; r < D.n; ++r) {
+            const long long k = order[r];
+            const long long q = D.off + r;
             cell[q] = D.cell_off + S.cell[k];
             id[q] = (int)k;
             if (f32) {
@@ -1009,8 +1031,9 @@ extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const doub
     if (!cl) {
         located.resize(D.n);
         for (long long k = 0; k < D.n; ++k) {
-            located[k] = host_locate(M, x[2 * k], x[2 * k + 1], -1);
-            if (located[k] < 0) return ctx->fail(FETDPIC_EOUTSIDE, "particle outside the mesh");
+            const int f = host_locate(M, x[2 * k], x[2 * k + 1], -1);
+            if (f < 0) return ctx->fail(FETDPIC_EOUTSIDE, "particle outside the mesh");
+            located[k] = M.perm[f];                  // the caller's index, as a given cell would be
         }
         cl = located.data();
     }
@@ -1023,7 +1046,7 @@ extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const doub
     CK(cudaMemcpyAsync(st + bx, u, bx, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(st + 2 * bx, cl, bc, cudaMemcpyHostToDevice, ctx->stream));
     launch_ingest(ctx->stream, D.n, D.off, D.cell_off, M.nf, ctx->p.precision == FETDPIC_FP32,
-                  (const double *)st, (const double *)(st + bx), (const int *)(st + 2 * bx), ctx->geo64,
+                  (const double *)st, (const double *)(st + bx), (const int *)(st + 2 * bx), ctx->tri_c2i, ctx->geo64,
                   1.0 / ctx->p.c, ctx->cell, ctx->id, ctx->f[0], ctx->f[1], ctx->f[2], ctx->f[3], ctx->status);
     CK(cudaGetLastError());
     if (!cell) CK(cudaStreamSynchronize(ctx->stream));   // `located` goes out of scope
@@ -1050,7 +1073,9 @@ extern "C" int fetdpic_write_fields(fetdpic_ctx *ctx, int inst, const double *e,
         CK(cudaStreamSynchronize(ctx->stream));
     }
     if (b) {
-        int rc = upload(ctx, ctx->b + ctx->cell_off[inst], b, (size_t)M.nf);
+        std::vector<double> bs(M.nf);                // stored triangle order
+        for (int f = 0; f < M.nf; ++f) bs[f] = b[M.perm[f]];
+        int rc = upload(ctx, ctx->b + ctx->cell_off[inst], bs.data(), bs.size());
         if (rc) return rc;
         CK(cudaStreamSynchronize(ctx->stream));
     }
@@ -1120,9 +1145,11 @@ extern "C" int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, do
     CK(cudaStreamSynchronize(ctx->stream));
     const HostMesh &M = ctx->mesh[inst];
     if (e) CK(cudaMemcpyAsync(e, ctx->e + ctx->edge_off[inst], sizeof(double) * M.ne, cudaMemcpyDeviceToHost, ctx->stream));
-    if (b) CK(cudaMemcpyAsync(b, ctx->b + ctx->cell_off[inst], sizeof(double) * M.nf, cudaMemcpyDeviceToHost, ctx->stream));
+    std::vector<double> bs(b ? M.nf : 0);
+    if (b) CK(cudaMemcpyAsync(bs.data(), ctx->b + ctx->cell_off[inst], sizeof(double) * M.nf, cudaMemcpyDeviceToHost, ctx->stream));
     if (j) CK(cudaMemcpyAsync(j, ctx->j + ctx->edge_off[inst], sizeof(double) * M.ne, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (b) for (int f = 0; f < M.nf; ++f) b[M.perm[f]] = bs[f];   // back to the caller's triangle order
     if (x || u || cell) {
         int rc = finalize(ctx);
         if (rc) return rc;
@@ -1137,10 +1164,10 @@ extern "C" int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, do
             if (ctx->p.precision == FETDPIC_FP32)
                 launch_unsort32(ctx->stream, ctx->P, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
                                 (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap,
-                                D.cell_off, ox, ou, oc);
+                                ctx->tri_i2c, ox, ou, oc);
             else
                 launch_unsort64(ctx->stream, ctx->P, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
-                                (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, D.cell_off, ox, ou, oc);
+                                (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, ctx->tri_i2c, ox, ou, oc);
             CK(cudaGetLastError());
             if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->stream));
             if (u) CK(cudaMemcpyAsync(u, ou, bx, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1229,7 +1256,7 @@ extern "C" int fetdpic_set_external_profile(fetdpic_ctx *ctx, int inst, const do
         for (int f = 0; f < nf; ++f) {
             if (!std::isfinite(w[2 * f]) || !std::isfinite(w[2 * f + 1]))
                 return ctx->fail(FETDPIC_EINVAL, "non-finite applied-field weight");
-            wv[f] = make_double2(w[2 * f], w[2 * f + 1]);
+            wv[ctx->mesh[inst].inv[f]] = make_double2(w[2 * f], w[2 * f + 1]);    // stored order
         }
     CK(cudaSetDevice(ctx->device));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -1563,11 +1590,11 @@ extern "C" int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, doub
     int *oc = (int *)(st + 2 * bx);
     if (ctx->p.precision == FETDPIC_FP32)
         launch_unsort32(ctx->stream, ctx->P, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
-                        (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap, D.cell_off,
+                        (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap, ctx->tri_i2c,
                         ox, ou, oc);
     else
         launch_unsort64(ctx->stream, ctx->P, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
-                        (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, D.cell_off, ox, ou, oc);
+                        (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, ctx->tri_i2c, ox, ou, oc);
     CK(cudaGetLastError());
     if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->stream));
     if (u) CK(cudaMemcpyAsync(u, ou, bx, cudaMemcpyDeviceToHost, ctx->stream));

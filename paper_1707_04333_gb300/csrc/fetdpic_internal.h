@@ -42,9 +42,19 @@ struct HostMesh {
     std::vector<long long> h_rp; std::vector<int> h_ci; std::vector<double> h_v;
     // SPAI M ~ [*eps]^-1, CSR with free-edge rows and edge-id columns
     std::vector<long long> m_rp; std::vector<int> m_ci; std::vector<double> m_v;
+    // triangle order: the library stores triangles along a Hilbert curve of their centroids;
+    // perm[internal] = the caller's index, inv[caller] = internal index
+    std::vector<int> perm, inv;
 };
 
+// Order of the triangles along a Hilbert curve of their centroids (ties by
+// index): perm[k] = the caller's index of the k-th triangle.  Neighbours end up
+// close in memory, so particles that have crossed into a neighbour since the
+// last sort, and the sort's scattered writes, stay within cached lines.
+std::vector<int> hilbert_order(int nn, const double *xy, int nf, const int *tri);
+
 // Returns 0 or a negative fetdpic_status; msg gets a reason on error.
+// tri: triangles in the caller's order; they are stored in hilbert_order.
 int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri,
                int ne_in, const int *edges_in, const int *tags_in,
                int n_per, const int *per_nodes, double tx, double ty, std::string &msg);
@@ -240,16 +250,19 @@ size_t scan_tmp_ints(long long n);
 void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n, int *tmp);
 
 // Host-layout particle state into a species range (FP32: barycentrics, u/c).
+// cell: the caller's instance-local triangle indices; c2i maps (cell_off +
+// caller index) to the internal instance-local index.
 void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, int nf, bool fp32, const double *x,
-                   const double *u, const int *cell, const Geo64 *geo, double inv_c, int *cell_o, int *id_o,
-                   void *f0, void *f1, void *f2, void *f3, unsigned *status);
+                   const double *u, const int *cell, const int *c2i, const Geo64 *geo, double inv_c, int *cell_o,
+                   int *id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status);
 
-// Particle state to load order (FP32 converts barycentrics to coordinates).
+// Particle state to load order (FP32 converts barycentrics to coordinates);
+// i2c maps an internal global triangle to the caller's instance-local index.
 void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
                      const double *y, const double *ux, const double *uy, long long off, long long cap,
-                     int cell_off, double *ox, double *ou, int *oc);
+                     const int *i2c, double *ox, double *ou, int *oc);
 void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
                      const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
-                     long long off, long long cap, int cell_off, double *ox, double *ou, int *oc);
+                     long long off, long long cap, const int *i2c, double *ox, double *ou, int *oc);
 
 }  // namespace fetdpic

@@ -302,9 +302,9 @@ void launch_sort(cudaStream_t st, const SortArgs &a)
 // An instance-local triangle outside [0, nf) is never used as an address: the
 // particle becomes padding and ST_BADCELL reports it at the next sync.
 __global__ void k_ingest(long long n, long long off, int cell_off, int nf, int fp32, const double *__restrict__ x,
-                         const double *__restrict__ u, const int *__restrict__ cell, const Geo64 *__restrict__ geo,
-                         double inv_c, int *__restrict__ cell_o, int *__restrict__ id_o, void *f0, void *f1,
-                         void *f2, void *f3, unsigned *status)
+                         const double *__restrict__ u, const int *__restrict__ cell, const int *__restrict__ c2i,
+                         const Geo64 *__restrict__ geo, double inv_c, int *__restrict__ cell_o,
+                         int *__restrict__ id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -316,7 +316,7 @@ __global__ void k_ingest(long long n, long long off, int cell_off, int nf, int f
         atomicOr(status, (unsigned)ST_BADCELL);
         return;
     }
-    const int c = cell_off + cl;
+    const int c = cell_off + c2i[cell_off + cl];
     cell_o[p] = c;
     id_o[p] = (int)k;
     const double px = x[2 * k], py = x[2 * k + 1];
@@ -337,17 +337,17 @@ __global__ void k_ingest(long long n, long long off, int cell_off, int nf, int f
 }
 
 void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, int nf, bool fp32, const double *x,
-                   const double *u, const int *cell, const Geo64 *geo, double inv_c, int *cell_o, int *id_o,
-                   void *f0, void *f1, void *f2, void *f3, unsigned *status)
+                   const double *u, const int *cell, const int *c2i, const Geo64 *geo, double inv_c, int *cell_o,
+                   int *id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status)
 {
     if (n <= 0) return;
-    k_ingest<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, cell_off, nf, fp32 ? 1 : 0, x, u, cell, geo,
+    k_ingest<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, cell_off, nf, fp32 ? 1 : 0, x, u, cell, c2i, geo,
                                                           inv_c, cell_o, id_o, f0, f1, f2, f3, status);
 }
 
 __global__ void k_unsort64(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,
                            const double *__restrict__ x, const double *__restrict__ y,
-                           const double *__restrict__ ux, const double *__restrict__ uy, int cell_off,
+                           const double *__restrict__ ux, const double *__restrict__ uy, const int *__restrict__ i2c,
                            double *__restrict__ ox, double *__restrict__ ou, int *__restrict__ oc)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,13 +358,13 @@ __global__ void k_unsort64(long long off, long long cap, const int *__restrict__
     const long long i = id[p];
     if (ox) { ox[2 * i] = x[p]; ox[2 * i + 1] = y[p]; }
     if (ou) { ou[2 * i] = ux[p]; ou[2 * i + 1] = uy[p]; }
-    if (oc) oc[i] = c - cell_off;
+    if (oc) oc[i] = i2c[c];
 }
 
 __global__ void k_unsort32(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,
                            const float *__restrict__ l0, const float *__restrict__ l1,
                            const float *__restrict__ ux, const float *__restrict__ uy,
-                           const Geo64 *__restrict__ geo, double c, int cell_off,
+                           const Geo64 *__restrict__ geo, double c, const int *__restrict__ i2c,
                            double *__restrict__ ox, double *__restrict__ ou, int *__restrict__ oc)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -381,25 +381,25 @@ __global__ void k_unsort32(long long off, long long cap, const int *__restrict__
         ox[2 * i + 1] = a * G.Y[0] + b * G.Y[1] + cc * G.Y[2];
     }
     if (ou) { ou[2 * i] = (double)ux[p] * c; ou[2 * i + 1] = (double)uy[p] * c; }
-    if (oc) oc[i] = f - cell_off;
+    if (oc) oc[i] = i2c[f];
 }
 
 void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
                      const double *y, const double *ux, const double *uy, long long off, long long cap,
-                     int cell_off, double *ox, double *ou, int *oc)
+                     const int *i2c, double *ox, double *ou, int *oc)
 {
     (void)P;
     if (cap <= 0) return;
-    k_unsort64<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, x, y, ux, uy, cell_off, ox, ou, oc);
+    k_unsort64<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, x, y, ux, uy, i2c, ox, ou, oc);
 }
 
 void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
                      const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
-                     long long off, long long cap, int cell_off, double *ox, double *ou, int *oc)
+                     long long off, long long cap, const int *i2c, double *ox, double *ou, int *oc)
 {
     (void)P;
     if (cap <= 0) return;
-    k_unsort32<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, l0, l1, ux, uy, geo, c, cell_off,
+    k_unsort32<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, l0, l1, ux, uy, geo, c, i2c,
                                                               ox, ou, oc);
 }
 

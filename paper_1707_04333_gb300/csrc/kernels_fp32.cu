@@ -472,7 +472,9 @@ __device__ __forceinline__ unsigned ring_slot(unsigned &qtail, bool walking, int
 
 // Segmented sum of v over runs of equal key across the warp (keys of a run are
 // adjacent: the particles are sorted by triangle); the run heads deposit the
-// sums with three integer atomics.
+// sums with three integer atomics.  (tests/test_run_reduction_model.py replays
+// this reduction, with the two-particle kernel's hand-off of first particles,
+// lane by lane on random warps.)
 __device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, int *v, int lane, const int *ew)
 {
     const unsigned full = 0xffffffffu;

@@ -22,12 +22,67 @@ static inline long long pair_key(int a, int b)
     return ((long long)lo << 32) | (unsigned)hi;
 }
 
-int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
+// Position of cell (x, y) of a 2^order x 2^order grid along the Hilbert curve
+// (the curve's recursive quadrant rule, one level per bit from the top).
+static unsigned long long hilbert_index(unsigned x, unsigned y, int order)
+{
+    const unsigned n = 1u << order;
+    unsigned long long d = 0;
+    for (unsigned s = n >> 1; s > 0; s >>= 1) {
+        const unsigned rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += (unsigned long long)s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {                       // reflect / transpose the quadrant so the curve stays continuous
+            if (rx == 1) { x = n - 1 - x; y = n - 1 - y; }
+            std::swap(x, y);
+        }
+    }
+    return d;
+}
+
+std::vector<int> hilbert_order(int nn, const double *xy, int nf, const int *tri)
+{
+    std::vector<int> perm(nf);
+    for (int f = 0; f < nf; ++f) perm[f] = f;
+    if (nf < 2) return perm;
+    double lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
+    std::vector<double> c(2 * (size_t)nf);
+    for (int f = 0; f < nf; ++f)
+        for (int d = 0; d < 2; ++d) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const int n = tri[3 * f + k];
+                v += (n >= 0 && n < nn) ? xy[2 * n + d] : 0.0;
+            }
+            c[2 * f + d] = v / 3.0;
+            lo[d] = std::min(lo[d], c[2 * f + d]);
+            hi[d] = std::max(hi[d], c[2 * f + d]);
+        }
+    const double span = std::max(hi[0] - lo[0], hi[1] - lo[1]);
+    const int order = 16;
+    const double scale = span > 0 ? ((1 << order) - 1) / span : 0.0;
+    std::vector<unsigned long long> key(nf);
+    for (int f = 0; f < nf; ++f) {
+        const unsigned x = (unsigned)((c[2 * f] - lo[0]) * scale), y = (unsigned)((c[2 * f + 1] - lo[1]) * scale);
+        key[f] = hilbert_index(x, y, order);
+    }
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    return perm;
+}
+
+int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_caller,
                int ne_in, const int *edges_in, const int *tags_in,
                int n_per, const int *per_nodes, double tx, double ty, std::string &msg)
 {
-    if (nn <= 0 || nf <= 0 || !xy || !tri_in) { msg = "empty mesh"; return FETDPIC_EINVAL; }
+    if (nn <= 0 || nf <= 0 || !xy || !tri_caller) { msg = "empty mesh"; return FETDPIC_EINVAL; }
     M.nn = nn; M.nf = nf;
+    // triangles are stored along the Hilbert curve; messages name the caller's indices
+    M.perm = hilbert_order(nn, xy, nf, tri_caller);
+    M.inv.assign(nf, 0);
+    for (int k = 0; k < nf; ++k) M.inv[M.perm[k]] = k;
+    std::vector<int> tri_store(3 * (size_t)nf);
+    for (int k = 0; k < nf; ++k)
+        for (int j = 0; j < 3; ++j) tri_store[3 * (size_t)k + j] = tri_caller[3 * (size_t)M.perm[k] + j];
+    const int *tri_in = tri_store.data();
     M.xy.assign(xy, xy + 2 * (size_t)nn);
     // periodic walls: each image node becomes its representative (Sec. III.C strip)
     M.rep.resize(nn);
@@ -56,11 +111,11 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
     for (int f = 0; f < nf; ++f) {
         int v[3] = {tri_in[3 * f], tri_in[3 * f + 1], tri_in[3 * f + 2]};
         for (int k = 0; k < 3; ++k)
-            if (v[k] < 0 || v[k] >= nn) { msg = "triangle " + std::to_string(f) + " has a node id out of range"; return FETDPIC_EMESH; }
-        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) { msg = "triangle " + std::to_string(f) + " repeats a node"; return FETDPIC_EMESH; }
+            if (v[k] < 0 || v[k] >= nn) { msg = "triangle " + std::to_string(M.perm[f]) + " has a node id out of range"; return FETDPIC_EMESH; }
+        if (v[0] == v[1] || v[1] == v[2] || v[0] == v[2]) { msg = "triangle " + std::to_string(M.perm[f]) + " repeats a node"; return FETDPIC_EMESH; }
         const double *p0 = &xy[2 * v[0]], *p1 = &xy[2 * v[1]], *p2 = &xy[2 * v[2]];
         double o = (p1[0] - p0[0]) * (p2[1] - p0[1]) - (p2[0] - p0[0]) * (p1[1] - p0[1]);
-        if (!(o != 0.0)) { msg = "triangle " + std::to_string(f) + " has zero area"; return FETDPIC_EMESH; }
+        if (!(o != 0.0)) { msg = "triangle " + std::to_string(M.perm[f]) + " has zero area"; return FETDPIC_EMESH; }
         if (o < 0.0) std::swap(v[1], v[2]);
         for (int k = 0; k < 3; ++k) M.tri[3 * f + k] = v[k];
     }
@@ -83,7 +138,7 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
         for (int f = 0; f < nf; ++f)
             for (int m = 0; m < 3; ++m) {
                 const int a = M.rep[M.tri[3 * f + (m + 1) % 3]], b = M.rep[M.tri[3 * f + (m + 2) % 3]];
-                if (a == b) { msg = "triangle " + std::to_string(f) + " joins a node to its periodic image"; return FETDPIC_EMESH; }
+                if (a == b) { msg = "triangle " + std::to_string(M.perm[f]) + " joins a node to its periodic image"; return FETDPIC_EMESH; }
                 keys.push_back(pair_key(a, b));
             }
         std::sort(keys.begin(), keys.end());
@@ -106,7 +161,7 @@ int build_mesh(HostMesh &M, int nn, const double *xy, int nf, const int *tri_in,
             int e;
             if (edges_in) {
                 auto it = given.find(k);
-                if (it == given.end()) { msg = "edge list misses an edge of triangle " + std::to_string(f); return FETDPIC_EMESH; }
+                if (it == given.end()) { msg = "edge list misses an edge of triangle " + std::to_string(M.perm[f]); return FETDPIC_EMESH; }
                 e = it->second;
             } else {
                 e = (int)(std::lower_bound(keys.begin(), keys.end(), k) - keys.begin());
@@ -267,12 +322,15 @@ void host_lambdas(const HostMesh &M, int f, double x, double y, double *l)
 
 int host_locate(const HostMesh &M, double x, double y, int hint)
 {
+    // hint and the scan are in the caller's triangle order; the result is the stored index
     double l[3];
     if (hint >= 0 && hint < M.nf) {
-        host_lambdas(M, hint, x, y, l);
-        if (l[0] >= 0.0 && l[1] >= 0.0 && l[2] >= 0.0) return hint;
+        const int f = M.inv[hint];
+        host_lambdas(M, f, x, y, l);
+        if (l[0] >= 0.0 && l[1] >= 0.0 && l[2] >= 0.0) return f;
     }
-    for (int f = 0; f < M.nf; ++f) {
+    for (int k = 0; k < M.nf; ++k) {
+        const int f = M.inv[k];
         host_lambdas(M, f, x, y, l);
         if (l[0] >= 0.0 && l[1] >= 0.0 && l[2] >= 0.0) return f;
     }
