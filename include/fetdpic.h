@@ -122,6 +122,11 @@ typedef struct {
                                 copies) before it gives up and reports FETDPIC_ETIMEOUT;
                                 0 = 2^20; negative = no poll, every such wait gives up at
                                 once (exercises the timeout path) */
+    int fuse_field_update;   /* 1 = the Ampere update (C^T [*mu^-1] b - i, then the SPAI
+                                product) runs as one cooperative launch whose blocks meet at a
+                                grid barrier with a bounded wait (FETDPIC_ETIMEOUT if it gives
+                                up); 0 = two launches (the default: measured faster on GB300).
+                                Same arithmetic, same results. */
 } fetdpic_params;
 
 /* One simulation instance (mesh + fields).  Instances share nothing but the
@@ -347,6 +352,10 @@ int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, int *row_ed
  * fetdpic_sync stays pending.  trial_steps <= 0 = 32.  The chosen values are returned in *variant and *sort_interval (each
  * may be NULL) and applied.  Blocks the calling thread. */
 int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, int *variant, int *sort_interval);
+
+/* Change wait_spin_limit of a live context (same meaning as in
+ * fetdpic_params); for steps enqueued after the call. */
+int fetdpic_set_wait_limit(fetdpic_ctx *ctx, long long wait_spin_limit);
 
 /* Apply a tuning found earlier (e.g. from a cache): variant 0 or 2-12;
  * sort_interval > 0, or < 0 for never. */

@@ -59,6 +59,7 @@ struct fetdpic_ctx {
     long long *m_soff = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
     float *m_v32 = nullptr, *r32 = nullptr;
     unsigned *status = nullptr;
+    unsigned *gbar = nullptr;                // grid-barrier state of the fused Ampere launch
     std::vector<double> unit_host;           // per instance (q_ref/dt) / scale
     std::vector<double> fixscale;            // per instance fixed-point scale (2^shift in FP64)
     std::vector<double> qunit_host;          // per instance charge of one fixed-point unit: q_ref / scale
@@ -457,6 +458,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
             ctx->m_v = ctx->alloc<double>(sv.size());
         }
         ctx->status = ctx->alloc<unsigned>(1);
+        ctx->gbar = ctx->alloc<unsigned>(2);
         if (P.check_interval > 0) {
             ctx->nrp = ctx->alloc<int>(nrp.size());
             ctx->nedge = ctx->alloc<int>(nedge.size());
@@ -771,6 +773,13 @@ static int finalize(fetdpic_ctx *ctx)
     return FETDPIC_OK;
 }
 
+// Polls per bounded wait inside a kernel: 0 = 2^20; negative = none (the wait gives up at once).
+static unsigned wait_polls(const fetdpic_ctx *ctx)
+{
+    const long long lim = ctx->p.wait_spin_limit;
+    return lim > 0 ? (unsigned)std::min<long long>(lim, 1ll << 30) : (lim < 0 ? 0u : (1u << 20));
+}
+
 static StepArgs64 args64(fetdpic_ctx *ctx)
 {
     StepArgs64 a{};
@@ -801,9 +810,7 @@ static StepArgs32 args32(fetdpic_ctx *ctx)
     a.rec_cap = ctx->p.record_walk; a.rec_cnt = ctx->rec_cnt; a.wrec = ctx->rec; a.id = ctx->id;
     a.edge_off = ctx->edge_off_dev;
     a.nblocks = ctx->nblocks; a.block = ctx->block;
-    // polls per bounded wait: 0 = 2^20; negative = none (the wait gives up at once)
-    const long long lim = ctx->p.wait_spin_limit;
-    a.spin = lim > 0 ? (unsigned)std::min<long long>(lim, 1ll << 30) : (lim < 0 ? 0u : (1u << 20));
+    a.spin = wait_polls(ctx);
     return a;
 }
 
@@ -894,8 +901,10 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     A.nfree = ctx->nfree; A.m_soff = ctx->m_soff; A.m_row = ctx->m_row; A.m_ci = ctx->m_ci; A.m_v = ctx->m_v;
     A.m_v32 = ctx->m_v32;
     A.e = ctx->e;
+    A.fused = ctx->p.fuse_field_update != 0;
+    A.gbar = ctx->gbar; A.spin = wait_polls(ctx); A.status = ctx->status;
     launch_ampere(ctx->stream, A);
-    launches += (ctx->E > 0) + (ctx->nfree > 0);
+    launches += A.fused ? (ctx->E > 0 || ctx->nfree > 0) : (ctx->E > 0) + (ctx->nfree > 0);
     if (ctx->probe_n > 0) {
         launch_probe(ctx->stream, ctx->probe_n, ctx->probe_w, ctx->e, ctx->probe_ring, ctx->probe_cap,
                      ctx->probe_count);
@@ -1384,6 +1393,15 @@ extern "C" int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, 
 static void drop_graphs(fetdpic_ctx *ctx)
 {
     for (auto &a : ctx->graph) for (auto &b : a) for (auto &g : b) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+extern "C" int fetdpic_set_wait_limit(fetdpic_ctx *ctx, long long wait_spin_limit)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->p.wait_spin_limit = wait_spin_limit;
+    drop_graphs(ctx);                          // captured steps hold the old limit
+    return FETDPIC_OK;
 }
 
 extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)

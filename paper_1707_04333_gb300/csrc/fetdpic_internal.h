@@ -207,6 +207,12 @@ struct AmpereArgs {
     // dt-scaled SPAI in sliced ELL: slice offsets, row -> edge, columns, values (FP64 or FP32)
     const long long *m_soff; const int *m_row; const int *m_ci; const double *m_v; const float *m_v32;
     double *e;
+    // one cooperative launch for both phases (fused = true): its grid barrier's state (zeroed by
+    // the launcher), the polls of its bounded wait, and the status word a wait that gives up sets
+    bool fused;
+    unsigned *gbar;
+    unsigned spin;
+    unsigned *status;
 };
 void launch_ampere(cudaStream_t st, const AmpereArgs &a);
 

@@ -1,5 +1,6 @@
 // Field-update (Ampere) kernels, the counting sort of particles by triangle,
 // the scan it needs, and the kernels that return particles in load order.
+#include <algorithm>
 #include <type_traits>
 
 #include <cuda_runtime.h>
@@ -50,73 +51,154 @@ template <> __device__ __forceinline__ double2 ld_keep<double2>(const double2 *p
     return v;
 }
 
-// r = C^T [*mu^-1] b^{n+1/2} - i^{n+1/2} on every edge (Eq. (semi.dis.curl.2)),
+// r = C^T [*mu^-1] b^{n+1/2} - i^{n+1/2} on edge e (Eq. (semi.dis.curl.2)),
 // with [*mu^-1] = 1/(mu0 A_f) folded into ecoef = s_f/(mu0 A_f).  The
 // fixed-point current is converted (unit = (q_ref/dt) 2^-shift per
 // instance), kept in j for reading, and cleared for the next step.  The dual
 // flux d += dt r accumulates for the Gauss-law check (d == NULL: checks off);
 // r (FP64) is stored for the FP64 SpMV, r32 for the FP32 one (either NULL).
-__global__ void k_curl_h(int E, const int2 *__restrict__ efac, const double2 *__restrict__ ecoef,
-                         const int *__restrict__ einst, const double *__restrict__ unit,
-                         const double *__restrict__ idt, const double *__restrict__ b,
-                         unsigned long long *__restrict__ ifix, double *__restrict__ r,
-                         float *__restrict__ r32, double *__restrict__ d, double *__restrict__ j)
+__device__ __forceinline__ void curl_h_edge(const AmpereArgs &a, int e, unsigned long long keep)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    const unsigned long long keep = l2_keep();
-    const int2 fa = ld_keep(efac + e, keep);
-    const double2 cf = ld_keep(ecoef + e, keep);
-    double h = b[fa.x] * cf.x;
-    if (fa.y >= 0) h += b[fa.y] * cf.y;
-    const int in = ld_keep(einst + e, keep);
-    const long long iv = (long long)ifix[e];
-    ifix[e] = 0ull;
-    const double cur = (double)iv * unit[in];
+    const int2 fa = ld_keep(a.efac + e, keep);
+    const double2 cf = ld_keep(a.ecoef + e, keep);
+    double h = a.b[fa.x] * cf.x;
+    if (fa.y >= 0) h += a.b[fa.y] * cf.y;
+    const int in = ld_keep(a.einst + e, keep);
+    const long long iv = (long long)a.ifix[e];
+    a.ifix[e] = 0ull;
+    const double cur = (double)iv * a.inst_unit[in];
     const double rv = h - cur;
-    if (r) r[e] = rv;
-    if (r32) r32[e] = (float)rv;
-    j[e] = cur;
-    if (d) d[e] += idt[in] * rv;
+    if (a.r) a.r[e] = rv;
+    if (a.r32) a.r32[e] = (float)rv;
+    a.j[e] = cur;
+    if (a.d) a.d[e] += a.inst_dt[in] * rv;
 }
 
-// e_free += (dt M) r: SpMV with the dt-scaled SPAI in sliced ELL (slices of
-// 32 rows, each padded to its longest row and stored column-major, so a warp
-// reads 32 consecutive column indices and values per step).  One thread per
-// row; padding entries have value 0 and a valid column.
+// e_free += (dt M) r for one row: SpMV with the dt-scaled SPAI in sliced ELL
+// (slices of 32 rows, each padded to its longest row and stored column-major,
+// so a warp of consecutive rows reads 32 consecutive column indices and values
+// per step).  Padding entries have value 0 and a valid column.  r is read
+// through the coherent path: the fused kernel writes it earlier in the launch.
 template <typename V>
-__global__ void __launch_bounds__(256) k_spai_sell(long long nrows, const long long *__restrict__ soff,
-                                                   const int *__restrict__ row_edge, const int *__restrict__ ci,
-                                                   const V *__restrict__ v, const V *__restrict__ r,
-                                                   double *__restrict__ e)
+__device__ __forceinline__ void spai_row(const AmpereArgs &a, const V *__restrict__ v, const V *r,
+                                         long long row, unsigned long long keep)
 {
-    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= nrows) return;
     const long long sl = row >> 5;
     const int lane = (int)(row & 31);
-    const long long o0 = soff[sl], o1 = soff[sl + 1];
-    const unsigned long long keep = l2_keep();
+    const long long o0 = a.m_soff[sl], o1 = a.m_soff[sl + 1];
     V s0 = V(0), s1 = V(0);
     long long q = o0 + lane;
     for (; q + 32 < o1; q += 64) {
-        s0 += ld_keep(v + q, keep) * r[ld_keep(ci + q, keep)];
-        s1 += ld_keep(v + q + 32, keep) * r[ld_keep(ci + q + 32, keep)];
+        s0 += ld_keep(v + q, keep) * r[ld_keep(a.m_ci + q, keep)];
+        s1 += ld_keep(v + q + 32, keep) * r[ld_keep(a.m_ci + q + 32, keep)];
     }
-    if (q < o1) s0 += ld_keep(v + q, keep) * r[ld_keep(ci + q, keep)];
-    e[row_edge[row]] += (double)(s0 + s1);
+    if (q < o1) s0 += ld_keep(v + q, keep) * r[ld_keep(a.m_ci + q, keep)];
+    a.e[a.m_row[row]] += (double)(s0 + s1);
+}
+
+__global__ void k_curl_h(AmpereArgs a)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.E) return;
+    curl_h_edge(a, e, l2_keep());
+}
+
+template <typename V>
+__global__ void __launch_bounds__(256) k_spai_sell(AmpereArgs a)
+{
+    const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.nfree) return;
+    if constexpr (sizeof(V) == 4) spai_row<float>(a, a.m_v32, a.r32, row, l2_keep());
+    else spai_row<double>(a, a.m_v, a.r, row, l2_keep());
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident): the last
+// block to arrive resets the count and advances the generation; the others
+// poll the generation at most `spin` times (sleeping briefly between polls)
+// and give up after that, setting ST_TIMEOUT, so no wait is unbounded.
+// Returns false in every thread of a block that gave up.
+__device__ __forceinline__ bool grid_sync(unsigned *gbar, unsigned spin, unsigned *status)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = gbar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
+            gbar[0] = 0u;
+            __threadfence();
+            atomicAdd(gbar + 1, 1u);
+        } else {
+            unsigned k = 0;
+            while (*gen == g) {
+                if (k++ >= spin) { ok = 0; atomicOr(status, (unsigned)ST_TIMEOUT); break; }
+                if (k > 4096) __nanosleep(32);           // busy first, then back off
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Both Ampere phases in one cooperative launch: r on every edge (grid-stride),
+// a grid barrier (the SpMV reads r anywhere), then e += dt M r on every free
+// row (grid-stride; a warp takes 32 consecutive rows, one slice).  Same
+// per-edge and per-row arithmetic as the two separate kernels, so the result
+// is bit-identical to them.
+constexpr int FUSED_BLOCK = 1024;              // one block per SM: few arrivals at the barrier
+
+template <typename V>
+__global__ void __launch_bounds__(FUSED_BLOCK) k_ampere_fused(AmpereArgs a)
+{
+    const unsigned long long keep = l2_keep();
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long e = tid; e < a.E; e += nth) curl_h_edge(a, (int)e, keep);
+    if (!grid_sync(a.gbar, a.spin, a.status)) return;
+    for (long long row = tid; row < a.nfree; row += nth) {
+        if constexpr (sizeof(V) == 4) spai_row<float>(a, a.m_v32, a.r32, row, keep);
+        else spai_row<double>(a, a.m_v, a.r, row, keep);
+    }
+}
+
+template <typename V>
+static void launch_fused(cudaStream_t st, const AmpereArgs &a)
+{
+    static int per_sm = 0, sms = 0, dev = -1;
+    int d = 0;
+    cudaGetDevice(&d);
+    if (d != dev || per_sm == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ampere_fused<V>, FUSED_BLOCK, 0);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
+        dev = d;
+        if (per_sm < 1) per_sm = 1;
+    }
+    const long long work = std::max<long long>(a.E, a.nfree);
+    const long long grid = std::min<long long>((work + FUSED_BLOCK - 1) / FUSED_BLOCK, (long long)per_sm * sms);
+    cudaMemsetAsync(a.gbar, 0, 2 * sizeof(unsigned), st);
+    AmpereArgs arg = a;
+    void *params[] = {&arg};
+    cudaLaunchCooperativeKernel((const void *)k_ampere_fused<V>, dim3((unsigned)grid), dim3(FUSED_BLOCK), params, 0,
+                                st);
 }
 
 void launch_ampere(cudaStream_t st, const AmpereArgs &a)
 {
-    if (a.E > 0)
-        k_curl_h<<<(a.E + 255) / 256, 256, 0, st>>>(a.E, a.efac, a.ecoef, a.einst, a.inst_unit, a.inst_dt,
-                                                     a.b, a.ifix, a.r, a.r32, a.d, a.j);
+    if (a.E <= 0 && a.nfree <= 0) return;
+    if (a.fused) {
+        if (a.m_v32) launch_fused<float>(st, a);
+        else launch_fused<double>(st, a);
+        return;
+    }
+    if (a.E > 0) k_curl_h<<<(a.E + 255) / 256, 256, 0, st>>>(a);
     if (a.nfree > 0) {
         const unsigned g = (unsigned)((a.nfree + 255) / 256);
-        if (a.m_v32)
-            k_spai_sell<float><<<g, 256, 0, st>>>(a.nfree, a.m_soff, a.m_row, a.m_ci, a.m_v32, a.r32, a.e);
-        else
-            k_spai_sell<double><<<g, 256, 0, st>>>(a.nfree, a.m_soff, a.m_row, a.m_ci, a.m_v, a.r, a.e);
+        if (a.m_v32) k_spai_sell<float><<<g, 256, 0, st>>>(a);
+        else k_spai_sell<double><<<g, 256, 0, st>>>(a);
     }
 }
 

@@ -484,11 +484,19 @@ __device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, i
     const int kp = __shfl_up_sync(full, key, 1);
     const bool head = (lane == 0) || (kp != key);
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
+    for (int off = 1; off < 16; off <<= 1) {
         const int o0 = __shfl_down_sync(full, v[0], off);
         const int o1 = __shfl_down_sync(full, v[1], off);
         const int o2 = __shfl_down_sync(full, v[2], off);
         if (lane + off <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
+    }
+    // the last level only when a run spans more than 16 lanes (rare: 32+ particles of one
+    // species in one triangle within a chunk)
+    if (__any_sync(full, seg_end - lane >= 16)) {
+        const int o0 = __shfl_down_sync(full, v[0], 16);
+        const int o1 = __shfl_down_sync(full, v[1], 16);
+        const int o2 = __shfl_down_sync(full, v[2], 16);
+        if (lane + 16 <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
     }
     if (head && key >= 0) add_seg32(ifix, ew, v);
 }

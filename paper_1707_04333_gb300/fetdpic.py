@@ -32,7 +32,7 @@ class Params(C.Structure):
                 ("block_size", C.c_int), ("use_graphs", C.c_int), ("time_stages", C.c_int), ("kernel_variant", C.c_int),
                 ("cuda_stream", C.c_void_p),
                 ("dev_alloc", _ALLOC), ("dev_free", _FREE), ("alloc_user", C.c_void_p),
-                ("wait_spin_limit", C.c_longlong)]
+                ("wait_spin_limit", C.c_longlong), ("fuse_field_update", C.c_int)]
 
 
 class Instance(C.Structure):
@@ -89,6 +89,7 @@ def lib():
             "fetdpic_stage_times": (i32, [vp, vp, vp]),
             "fetdpic_autotune": (i32, [vp, i32, i32, vp, vp]),
             "fetdpic_set_tuning": (i32, [vp, i32, i32]),
+            "fetdpic_set_wait_limit": (i32, [vp, i64]),
             "fetdpic_particle_bytes": (i32, [vp, vp, vp]),
             "fetdpic_fma_rate": (i32, [i32, vp]),
             "fetdpic_last_error": (C.c_char_p, [vp]),
@@ -264,6 +265,10 @@ def fetdpic_set_tuning(h, variant, sort_interval):
     return _check(h, lib().fetdpic_set_tuning(h, variant, sort_interval))
 
 
+def fetdpic_set_wait_limit(h, limit):
+    return _check(h, lib().fetdpic_set_wait_limit(h, int(limit)))
+
+
 def fetdpic_particle_bytes(h):
     b = C.c_double()
     n = C.c_longlong()
@@ -307,7 +312,7 @@ class Simulation:
     def __init__(self, workloads, precision="fp64", spai_level=2, sort_interval=16, max_crossings=64,
                  record_walk=0, block_size=0, check_interval=0, use_torch=True, stream=None,
                  edges=None, edge_tags=None, time_stages=False, kernel_variant=0, use_graphs=False,
-                 wait_spin_limit=0):
+                 wait_spin_limit=0, fuse_field_update=False):
         if not isinstance(workloads, (list, tuple)):
             workloads = [workloads]
         self.workloads = list(workloads)
@@ -324,6 +329,7 @@ class Simulation:
         p.kernel_variant = kernel_variant
         p.use_graphs = 1 if use_graphs else 0
         p.wait_spin_limit = wait_spin_limit
+        p.fuse_field_update = 1 if fuse_field_update else 0
         self.stream = None
         if use_torch:
             import torch

@@ -247,6 +247,7 @@ def test_forced_timeout_reports_and_context_recovers(fx):
         fetdpic.fetdpic_sync(sim.h)
     assert ei.value.code == fetdpic.ETIMEOUT
     fetdpic.fetdpic_sync(sim.h)                        # reported once
+    fetdpic.fetdpic_set_wait_limit(sim.h, 0)           # back to the default bound
     for k in range(2):
         fetdpic.fetdpic_write_particles(sim.h, k, ck[k]["x"], ck[k]["u"], ck[k]["cell"])
     fetdpic.fetdpic_write_fields(sim.h, 0, fck["e"], fck["b"])
@@ -264,3 +265,39 @@ def test_forced_timeout_reports_and_context_recovers(fx):
     assert np.array_equal(sim.read_fields()["e"], ref.read_fields()["e"])
     sim.close()
     ref.close()
+
+
+def test_field_update_grid_barrier_timeout_and_recovery(fx):
+    """The fused Ampere update's cooperative launch meets at a grid barrier whose wait is bounded:
+    with no poll allowed the waiting blocks give up and fetdpic_sync reports FETDPIC_ETIMEOUT once;
+    with the default bound restored, the same context steps normally."""
+    fetdpic, oracle = fx
+    w = inputs.pair_plasma(24, 6, kT=0.1, wc_over_wp=0.5, seed=28, pusher="vay")
+    for prec in ("fp64", "fp32"):
+        sim = fetdpic.Simulation(w, precision=prec, spai_level=1, sort_interval=-1, wait_spin_limit=-1,
+                                 fuse_field_update=True).load()
+        fetdpic.fetdpic_step(sim.h, 1, "vay")
+        with pytest.raises(fetdpic.FetdpicError) as ei:
+            fetdpic.fetdpic_sync(sim.h)
+        assert ei.value.code == fetdpic.ETIMEOUT, prec
+        fetdpic.fetdpic_set_wait_limit(sim.h, 0)
+        sim.step(2, "vay").sync()
+        sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_field_update_equals_two_launches(fx, precision):
+    """One cooperative launch for C^T H b - i and the SPAI product gives bit-identical fields,
+    current and particles to the two separate launches, over steps with sorts."""
+    fetdpic, oracle = fx
+    w = inputs.pair_plasma(20, 8, kT=0.2, wc_over_wp=0.5, seed=29, pusher="hc")
+    out = []
+    for fuse in (True, False):
+        sim = fetdpic.Simulation(w, precision=precision, spai_level=2, sort_interval=3,
+                                 fuse_field_update=fuse).load()
+        sim.step(7, "hc").sync()
+        out.append((sim.read_fields(), sim.read_species(0), sim.read_species(1)))
+        sim.close()
+    for a, b in zip(out[0], out[1]):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), k
