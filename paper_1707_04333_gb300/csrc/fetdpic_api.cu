@@ -683,7 +683,8 @@ static int finalize(fetdpic_ctx *ctx)
         const Species &D = ctx->sp[s];
         Sp32 &T = s32[s];
         // the FP32 path takes the applied fields from the per-triangle field record
-        T.kappa = D.kappa; T.xe_x = 0.0f; T.xe_y = 0.0f; T.xb = 0.0f;
+        T = Sp32{};
+        T.kappa = D.kappa;
         T.wfix = (float)D.wfix;
         T.inst = D.inst; T.edge_off = ctx->edge_off[D.inst]; T.off = (int)D.off;
     }

@@ -97,13 +97,15 @@ static_assert(sizeof(CstA) == 32, "CstA layout");
 struct __align__(8) CstB { int ew0, nb2; };
 static_assert(sizeof(CstB) == 8, "CstB layout");
 
-// FP32-path species parameters, read with uniform loads (32 B).
+// FP32-path species parameters (32 B): q/m and the fixed-point weight first,
+// read by the particle pass in one 8-byte uniform load.  Applied fields reach
+// the FP32 path through the per-triangle field record, not through here.
 struct __align__(16) Sp32 {
     float kappa;                            // q/m
-    float xe_x, xe_y, xb;                   // external fields pre-scaled (alpha E/c, alpha B)
     float wfix;                             // (q / q_ref) * (2^25 - 64)
     int inst, edge_off;
     int off;                                // storage offset of the species (walk record index base)
+    int pad[3];
 };
 static_assert(sizeof(Sp32) == 32, "Sp32 layout");
 

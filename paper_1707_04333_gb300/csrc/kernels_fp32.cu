@@ -418,16 +418,16 @@ struct POne {
 // current of a particle that stays in its triangle (Eq. (I.assign), written
 // i_ab += (Q/dt)(l_a dl_b - dl_a l_b)).
 template <int PUSHER>
-__device__ __forceinline__ POne one_particle(const float4 &s0, float wfix, int f, float l0, float l1, float ux,
+__device__ __forceinline__ POne one_particle(float kappa, float wfix, int f, float l0, float l1, float ux,
                                              float uy, const PRec &r)
 {
     POne o;
     const bool live = f >= 0;
     const float l2 = 1.f - l0 - l1;
     // alpha E / c = (q/m) sum_n l_n V_n, beta = (q/m) B_z dt/2
-    const float ex = s0.x * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x) + s0.y;
-    const float ey = s0.x * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y) + s0.z;
-    const float bz = s0.x * r.r1.z + s0.w;
+    const float ex = kappa * (l0 * r.r0.x + l1 * r.r0.z + l2 * r.r1.x);
+    const float ey = kappa * (l0 * r.r0.y + l1 * r.r0.w + l2 * r.r1.y);
+    const float bz = kappa * r.r1.z;
     float ig, vx, vy;
     if (1.f + ux * ux + uy * uy > 100.f) {
         const PushOut q = push_fp64<PUSHER>(ux, uy, ex, ey, bz);
@@ -484,19 +484,21 @@ __device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, i
     const int kp = __shfl_up_sync(full, key, 1);
     const bool head = (lane == 0) || (kp != key);
 #pragma unroll
-    for (int off = 1; off < 16; off <<= 1) {
+    for (int off = 1; off < 4; off <<= 1) {
         const int o0 = __shfl_down_sync(full, v[0], off);
         const int o1 = __shfl_down_sync(full, v[1], off);
         const int o2 = __shfl_down_sync(full, v[2], off);
         if (lane + off <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
     }
-    // the last level only when a run spans more than 16 lanes (rare: 32+ particles of one
-    // species in one triangle within a chunk)
-    if (__any_sync(full, seg_end - lane >= 16)) {
-        const int o0 = __shfl_down_sync(full, v[0], 16);
-        const int o1 = __shfl_down_sync(full, v[1], 16);
-        const int o2 = __shfl_down_sync(full, v[2], 16);
-        if (lane + 16 <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
+    // the levels 4, 8, 16 only when some run spans more lanes than that (a warp vote):
+    // sorted runs are about 10 lanes long, and drifted particles make them shorter
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+        if (!__any_sync(full, seg_end - lane >= off)) break;
+        const int o0 = __shfl_down_sync(full, v[0], off);
+        const int o1 = __shfl_down_sync(full, v[1], off);
+        const int o2 = __shfl_down_sync(full, v[2], off);
+        if (lane + off <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
     }
     if (head && key >= 0) add_seg32(ifix, ew, v);
 }
@@ -510,9 +512,8 @@ __device__ __forceinline__ void process_chunk(const StepArgs32 &a, unsigned c, i
 {
     const unsigned p = c * 32u + (unsigned)lane;
     const Sp32 *spp = a.sp + s.sp;
-    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
-    const float wfix = __ldg(&spp->wfix);
-    POne o = one_particle<PUSHER>(s0, wfix, s.f, s.l0, s.l1, s.ux, s.uy, r);
+    const float2 kw = __ldg(reinterpret_cast<const float2 *>(spp));      // q/m, fixed-point weight
+    POne o = one_particle<PUSHER>(kw.x, kw.y, s.f, s.l0, s.l1, s.ux, s.uy, r);
     if (o.bad) atomicOr(a.status, (unsigned)ST_NONFINITE);
     {
         const unsigned slot = ring_slot(qtail, o.walking, lane);
@@ -615,9 +616,8 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     const unsigned full = 0xffffffffu;
     const unsigned pa = c * 64u + 2u * (unsigned)lane;
     const Sp32 *spp = a.sp + s.sp;
-    const float4 s0 = __ldg(reinterpret_cast<const float4 *>(spp));
-    const float wfix = __ldg(&spp->wfix);
-    const POne A = one_particle<PUSHER>(s0, wfix, s.fa, s.l0.x, s.l1.x, s.ux.x, s.uy.x, ra);
+    const float2 kw = __ldg(reinterpret_cast<const float2 *>(spp));      // q/m, fixed-point weight
+    const POne A = one_particle<PUSHER>(kw.x, kw.y, s.fa, s.l0.x, s.l1.x, s.ux.x, s.uy.x, ra);
     {
         const unsigned slot = ring_slot(qtail, A.walking, lane);
         if (A.walking) q[slot & (P32_QUEUE2 - 1)] = walk_item(pa, s.fa, s.sp, s.l0.x, s.l1.x, A);
@@ -630,7 +630,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     } else {
         rb = rb_in;
     }
-    const POne B = one_particle<PUSHER>(s0, wfix, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
+    const POne B = one_particle<PUSHER>(kw.x, kw.y, s.fb, s.l0.y, s.l1.y, s.ux.y, s.uy.y, rb);
     {
         const unsigned slot = ring_slot(qtail, B.walking, lane);
         if (B.walking) q[slot & (P32_QUEUE2 - 1)] = walk_item(pa + 1, s.fb, s.sp, s.l0.y, s.l1.y, B);
