@@ -534,7 +534,7 @@ def main():
 
     # ---- measured arithmetic peaks (the FP64 path is bound by the FP64 rate)
     arith = None
-    if rank == 0:
+    if rank == 0 and not args.no_fp64:
         arith = {"fp32_tflops": fetdpic.fetdpic_fma_rate(False), "fp64_tflops": fetdpic.fetdpic_fma_rate(True),
                  "how": "FMA chains filling every SM, CUDA events, best launch of >= 20 ms"}
 
