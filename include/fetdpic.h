@@ -111,8 +111,13 @@ typedef struct {
                                 blocks, 7 per SM; 7 = 64-thread blocks, 14 per SM.  Two adjacent
                                 particles per thread: 8 = 256-thread blocks, 9 = 128, 10 = 64;
                                 11 = 128 and 12 = 64 with the two particles' triangle records read
-                                one after the other (fewer registers, 24 warps per SM).
-                                0 = default (10).  All give identical results. */
+                                one after the other (fewer registers, 24 warps per SM).  With a
+                                per-block deposit window in shared memory (the current of
+                                triangles near the block's particles summed there and added to
+                                the global current once per block): 13 and 14 = variant 10 with
+                                320- and 256-triangle windows, 15 = variant 12 with 192, 16 =
+                                variant 9 with 640.  0 = default (10).  All give identical
+                                results.  Other values: FETDPIC_EINVAL. */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);

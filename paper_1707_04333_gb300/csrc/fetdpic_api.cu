@@ -231,6 +231,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.record_walk < 0) return FETDPIC_EINVAL;
     // untuned FP32 default: two particles per thread in 64-thread blocks (20 warps per SM at 96
     // registers), measured fastest on the benchmark workload
+    if (P.kernel_variant < 0 || P.kernel_variant == 1 || P.kernel_variant > 16) return FETDPIC_EINVAL;
     if (P.kernel_variant == 0) P.kernel_variant = 10;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
@@ -1408,7 +1409,7 @@ extern "C" int fetdpic_set_wait_limit(fetdpic_ctx *ctx, long long wait_spin_limi
 extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)
 {
     if (!ctx) return FETDPIC_EINVAL;
-    if (variant < 0 || variant > 12 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
+    if (variant < 0 || variant > 16 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->p.kernel_variant = variant == 0 ? 10 : variant;    // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
@@ -1459,7 +1460,7 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     ctx->p.check_interval = 0;
     ctx->probe_n = 0;
     rc = copy_state(true);
-    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12} : std::vector<int>{3};
+    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 14} : std::vector<int>{3};
     std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 12, 16, 32};
     double best = 1e300;
     int bv = keep_variant, bs = keep_sort;

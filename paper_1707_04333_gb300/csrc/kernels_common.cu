@@ -287,16 +287,37 @@ void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n
 // of particles inside one triangle depends on atomic order; nothing computed
 // depends on it (the deposit is integer, reads go through the id array).
 
+// Runs of equal key among the lanes of a warp (adjacent lanes only: the
+// particles are nearly sorted, so runs are long; a key that comes back later
+// in the warp starts a run of its own).  head: first lane of its run; lead:
+// that run's first lane; len: the run's length (valid on its first lane).
+struct WarpRun { bool head; int lead, len; };
+__device__ __forceinline__ WarpRun warp_run(int key, int lane)
+{
+    const unsigned full = 0xffffffffu;
+    const int kn = __shfl_down_sync(full, key, 1);
+    const int kp = __shfl_up_sync(full, key, 1);
+    const unsigned tails = __ballot_sync(full, lane == 31 || kn != key);
+    const bool head = lane == 0 || kp != key;
+    const unsigned heads = __ballot_sync(full, head);
+    WarpRun r;
+    r.head = head;
+    r.lead = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    r.len = __ffs(tails >> lane);
+    return r;
+}
+
 // Histogram: one integer atomic per run of equal triangle in a warp.
 __global__ void k_hist(const int *__restrict__ cell, const short *__restrict__ blk_sp, const Species *__restrict__ sp,
                        const int *__restrict__ hoff, int *__restrict__ hist)
 {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const int c = cell[p];
     const int s = blk_sp[blockIdx.x];
     const int slot = c < 0 ? -1 : hoff[s] + (c - sp[s].cell_off);
-    const unsigned peers = __match_any_sync(0xffffffffu, slot);
-    if (slot >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(hist + slot, __popc(peers));
+    const WarpRun r = warp_run(slot, lane);
+    if (slot >= 0 && r.head) atomicAdd(hist + slot, r.len);
 }
 
 // Scatter through per-triangle cursors.  Each warp handles SC_CHUNKS

@@ -201,6 +201,30 @@ __device__ __forceinline__ void seg_current32(const float *ls, const float *lf, 
     }
 }
 
+// Deposit window of a block: fixed-point current of the local edges of the
+// triangles [t0, t0 + nt), in global orientation, slot m * WT + (f - t0) for
+// local edge m of triangle f.  A value s (|s| < 2^31) goes in as two 32-bit
+// shared-memory atomics, its low 16 bits (unsigned) and s >> 16 (signed), so
+// s = hi 2^16 + lo exactly; the block adds hi 2^16 + lo of every non-zero slot
+// to the global current once, after all its warps are done.  Each addition into
+// a slot stands for at least one particle of the block, so with at most 2^16
+// particles per block neither sum overflows: sum lo < 2^16 (2^16 - 1) < 2^32,
+// |sum hi| <= 2^16 2^15.  Deposits into other triangles, and those of the
+// walk, go to the global current directly.  Integer sums: the result is the
+// same either way.  nt = 0: no window (every deposit is global).
+struct DepWin { unsigned lo, hi; int t0, nt; };        // lo, hi: shared-memory addresses
+
+// Shared-memory reductions, written as such (the window is reached through a
+// structure, so a generic atomic would otherwise be possible).
+__device__ __forceinline__ void red_shared_u32(unsigned addr, unsigned v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+__device__ __forceinline__ void red_shared_s32(unsigned addr, int v)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
 // Three integer atomics, issued whatever their value (adding 0 changes nothing,
 // and a test would cost a divergent branch per edge).
 __device__ __forceinline__ void add_seg32(unsigned long long *ifix, const int *ew, const int *v)
@@ -209,6 +233,33 @@ __device__ __forceinline__ void add_seg32(unsigned long long *ifix, const int *e
     for (int m = 0; m < 3; ++m) {
         const long long s = (ew[m] & 1) ? -(long long)v[m] : (long long)v[m];
         atomicAdd(ifix + (ew[m] >> 1), (unsigned long long)s);
+    }
+}
+
+// The deposit of a lane with `dep` set into triangle f, called by the whole
+// (converged) warp: into the window when f is in it, else to the global
+// current; a warp vote skips a path no lane takes.
+template <int WT>
+__device__ __forceinline__ void add_seg32w(unsigned long long *ifix, const DepWin &w, bool dep, int f,
+                                           const int *ew, const int *v)
+{
+    if constexpr (WT > 0) {
+        const unsigned full = 0xffffffffu;
+        const int r = f - w.t0;
+        const bool in = dep && (unsigned)r < (unsigned)w.nt;
+        if (__any_sync(full, in) && in) {
+            const unsigned o = 4u * (unsigned)r;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const int s = (ew[m] & 1) ? -v[m] : v[m];
+                red_shared_u32(w.lo + o + 4u * m * WT, (unsigned)s & 0xffffu);
+                red_shared_s32(w.hi + o + 4u * m * WT, s >> 16);
+            }
+        }
+        const bool out = dep && !in;
+        if (__any_sync(full, out) && out) add_seg32(ifix, ew, v);
+    } else {
+        if (dep) add_seg32(ifix, ew, v);
     }
 }
 
@@ -475,7 +526,9 @@ __device__ __forceinline__ unsigned ring_slot(unsigned &qtail, bool walking, int
 // sums with three integer atomics.  (tests/test_run_reduction_model.py replays
 // this reduction, with the two-particle kernel's hand-off of first particles,
 // lane by lane on random warps.)
-__device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, int *v, int lane, const int *ew)
+template <int WT = 0>
+__device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, int *v, int lane, const int *ew,
+                                            const DepWin &w = DepWin{})
 {
     const unsigned full = 0xffffffffu;
     const int kn = __shfl_down_sync(full, key, 1);
@@ -500,7 +553,7 @@ __device__ __forceinline__ void run_deposit(unsigned long long *ifix, int key, i
         const int o2 = __shfl_down_sync(full, v[2], off);
         if (lane + off <= seg_end) { v[0] += o0; v[1] += o1; v[2] += o2; }
     }
-    if (head && key >= 0) add_seg32(ifix, ew, v);
+    add_seg32w<WT>(ifix, w, head && key >= 0, key, ew, v);
 }
 
 // One 32-particle chunk, one particle per lane: gather, push, in-triangle
@@ -608,10 +661,10 @@ __device__ __forceinline__ PState2 load_state2(const StepArgs32 &a, unsigned c, 
 // arithmetic (a compiler barrier keeps them there), so the two record sets are
 // never live together; when both particles share a triangle the second load
 // hits L1.
-template <int PUSHER, bool SEQ>
+template <int PUSHER, bool SEQ, int WT>
 __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, int lane, const PState2 &s,
                                                const PRec &ra, const PRec &rb_in, WalkItem *q, unsigned &qhead,
-                                               unsigned &qtail, bool &bad)
+                                               unsigned &qtail, bool &bad, const DepWin &dw)
 {
     const unsigned full = 0xffffffffu;
     const unsigned pa = c * 64u + 2u * (unsigned)lane;
@@ -645,7 +698,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     const int okey = same ? -1 : A.key;                  // orphan's triangle, -1: none
     const int kp = __shfl_up_sync(full, key, 1);
     const bool given = lane > 0 && okey >= 0 && okey == kp;
-    if (okey >= 0 && !given) add_seg32(a.ifix, ewa, A.v);
+    add_seg32w<WT>(a.ifix, dw, okey >= 0 && !given, okey, ewa, A.v);
     int v0[3];
     {
         const bool taken = __shfl_down_sync(full, given, 1) && lane < 31;
@@ -657,7 +710,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     }
     {
         const int ewb[3] = {__float_as_int(rb.r1.w), __float_as_int(rb.c1.x), __float_as_int(rb.c1.y)};
-        run_deposit(a.ifix, key, v0, lane, ewb);
+        run_deposit<WT>(a.ifix, key, v0, lane, ewb, dw);
     }
     // state: both slots of every lane are written.  A walker's position is rewritten by its
     // walk after the warp barrier below, and its momentum (stored here as pushed) only if a
@@ -682,10 +735,17 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
     }
 }
 
-template <int PUSHER, int MINB, int NW, bool SEQ>
+// WT > 0: the block's deposit window holds WT triangles centred on the
+// triangle of the particle in the middle of the block's chunk range (the warps
+// of a block take adjacent ranges of sorted particles, so their triangles, in
+// Hilbert order, are a compact patch of the mesh; the window also catches most
+// particles that have moved to a neighbour since the sort).
+template <int PUSHER, int MINB, int NW, bool SEQ, int WT = 0>
 __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
 {
     __shared__ WalkItem qbuf[NW][P32_QUEUE2];
+    __shared__ unsigned wlo[WT > 0 ? 3 * WT : 1];
+    __shared__ int whi[WT > 0 ? 3 * WT : 1];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WalkItem *q = qbuf[warp];
     unsigned qhead = 0, qtail = 0;
@@ -695,19 +755,55 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
     const unsigned K = (unsigned)((n64 + nwarps - 1) / nwarps);
     unsigned c = wid * K;
     const unsigned cend = (unsigned)min((long long)c + K, n64);
-    if (c >= cend) return;
-    bool bad = false;
-    PState2 sn = load_state2(a, c, lane);
-    for (; c < cend; ++c) {
-        const PState2 s = sn;
-        if (c + 1 < cend) sn = load_state2(a, c + 1, lane);
-        const PRec ra = load_rec(a, s.fa);
-        PRec rb;
-        if (!SEQ) rb = load_rec(a, s.fb);
-        process_chunk2<PUSHER, SEQ>(a, c, lane, s, ra, rb, q, qhead, qtail, bad);
+    PState2 sn;
+    if (c < cend) sn = load_state2(a, c, lane);            // in flight while the window is set up
+    DepWin dw{(unsigned)__cvta_generic_to_shared(wlo), (unsigned)__cvta_generic_to_shared(whi), 0, 0};
+    if (WT > 0) {
+        for (int i = threadIdx.x; i < 3 * WT; i += NW * 32) { wlo[i] = 0u; whi[i] = 0; }
+        const long long b0 = (long long)blockIdx.x * NW * K, b1 = min(b0 + (long long)NW * K, n64);
+        int tc = -1;
+        if (b0 < b1 && (long long)NW * K * 64 <= 65536) {       // the window's sums cannot overflow
+            tc = a.cell[((b0 + b1) / 2) * 64];
+            if (tc < 0) tc = a.cell[b0 * 64];            // middle chunk in a species' padding
+        }
+        dw.t0 = tc - WT / 2;
+        dw.nt = tc >= 0 ? WT : 0;
+        __syncthreads();
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
-    drain<P32_QUEUE2>(a, q, qhead, qtail, lane);
+    if (c < cend) {
+        bool bad = false;
+        for (; c < cend; ++c) {
+            const PState2 s = sn;
+            if (c + 1 < cend) sn = load_state2(a, c + 1, lane);
+            const PRec ra = load_rec(a, s.fa);
+            PRec rb;
+            if (!SEQ) rb = load_rec(a, s.fb);
+            process_chunk2<PUSHER, SEQ, WT>(a, c, lane, s, ra, rb, q, qhead, qtail, bad, dw);
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(a.status, (unsigned)ST_NONFINITE);
+        drain<P32_QUEUE2>(a, q, qhead, qtail, lane);
+    }
+    if constexpr (WT > 0) {
+        // a non-zero slot belongs to a triangle some particle was deposited in, so t is valid;
+        // all edge words are loaded before the first atomic, so the flush waits for one load
+        constexpr int NIT = 3 * WT / (NW * 32);
+        static_assert(NIT * NW * 32 == 3 * WT, "window slots per thread");
+        __syncthreads();
+        long long v[NIT];
+        int ew[NIT];
+#pragma unroll
+        for (int k = 0; k < NIT; ++k) {
+            const int i = threadIdx.x + k * NW * 32;
+            v[k] = (long long)whi[i] * 65536 + (long long)wlo[i];
+            const int m = i / WT, t = dw.t0 + (i - m * WT);
+            ew[k] = 0;
+            if (v[k] != 0)
+                ew[k] = m == 0 ? __ldg(&a.cstb[t].ew0) : (m == 1 ? __ldg(&a.csta[t].ew1) : __ldg(&a.csta[t].ew2));
+        }
+#pragma unroll
+        for (int k = 0; k < NIT; ++k)
+            if (v[k] != 0) atomicAdd(a.ifix + (ew[k] >> 1), (unsigned long long)v[k]);
+    }
 }
 
 // ------------------------------------------------------- staged variant
@@ -867,14 +963,14 @@ static void launch_p32(cudaStream_t st, const StepArgs32 &a)
     k_particles32<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
 }
 
-template <int PUSHER, int MINB, int NW, bool SEQ = false>
+template <int PUSHER, int MINB, int NW, bool SEQ = false, int WT = 0>
 static void launch_p32x2(cudaStream_t st, const StepArgs32 &a)
 {
     static int per_sm = 0, sms = 0, dev = -1;
     int d = 0;
     cudaGetDevice(&d);
     if (d != dev || per_sm == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32x2<PUSHER, MINB, NW, SEQ>, NW * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles32x2<PUSHER, MINB, NW, SEQ, WT>, NW * 32, 0);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d);
         dev = d;
         if (per_sm < 1) per_sm = 1;
@@ -882,7 +978,7 @@ static void launch_p32x2(cudaStream_t st, const StepArgs32 &a)
     const long long need = (a.nchunks / 2 + NW - 1) / NW;
     const long long grid = std::min<long long>(need, (long long)per_sm * sms);
     if (grid <= 0) return;
-    k_particles32x2<PUSHER, MINB, NW, SEQ><<<(unsigned)grid, NW * 32, 0, st>>>(a);
+    k_particles32x2<PUSHER, MINB, NW, SEQ, WT><<<(unsigned)grid, NW * 32, 0, st>>>(a);
 }
 
 template <int PUSHER>
@@ -915,6 +1011,10 @@ static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
     case 10: launch_p32x2<PUSHER, 10, 2>(st, a); break;
     case 11: launch_p32x2<PUSHER, 6, 4, true>(st, a); break;
     case 12: launch_p32x2<PUSHER, 12, 2, true>(st, a); break;
+    case 13: launch_p32x2<PUSHER, 10, 2, false, 320>(st, a); break;
+    case 14: launch_p32x2<PUSHER, 10, 2, false, 256>(st, a); break;
+    case 15: launch_p32x2<PUSHER, 12, 2, true, 192>(st, a); break;
+    case 16: launch_p32x2<PUSHER, 5, 4, false, 640>(st, a); break;
     case 2: launch_p32<PUSHER, 2>(st, a); break;
     case 4: launch_p32<PUSHER, 4>(st, a); break;
     default: launch_p32<PUSHER, 3>(st, a); break;     // measured best on GB300 (no spills, 24 warps/SM)

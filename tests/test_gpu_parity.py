@@ -223,13 +223,14 @@ def test_graph_replay_equals_plain_launches(fx, precision):
 
 def test_fp32_kernel_variants_bit_identical(fx):
     """Every FP32 particle-kernel variant (register prefetch at 2, 3 or 4 resident blocks per SM;
-    shared-memory staging by bulk asynchronous copies) computes the same per-particle arithmetic
-    and integer deposits, so all give bit-identical particles and fields over steps with walks,
-    wall reflections, sorts and all three pushers, on enough particles for many chunks per warp."""
+    shared-memory staging by bulk asynchronous copies; two particles per thread; per-block
+    deposit windows in shared memory) computes the same per-particle arithmetic and integer
+    deposits, so all give bit-identical particles and fields over steps with walks, wall
+    reflections, sorts and all three pushers, on enough particles for many chunks per warp."""
     fetdpic, _ = fx
     w = inputs.pair_plasma(48, 24, kT=0.3, seed=23, pusher="vay")
     outs = {}
-    for v in (3, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12):
+    for v in (3, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16):
         s = fetdpic.Simulation(w, precision="fp32", spai_level=1, sort_interval=4, kernel_variant=v,
                                check_interval=5).load()
         s.step(5, "vay").step(4, "hc").step(6, "boris").sync()
@@ -237,7 +238,7 @@ def test_fp32_kernel_variants_bit_identical(fx):
         assert c["dce"] < 2e-5, (v, c)
         outs[v] = (s.read_fields(), s.read_species(0), s.read_species(1))
         s.close()
-    for v in (2, 4, 5, 6, 7, 8, 9, 10, 11, 12):
+    for v in (2, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16):
         for a, b in zip(outs[3], outs[v]):
             for k in a:
                 assert np.array_equal(a[k], b[k]), (v, k)
@@ -253,7 +254,7 @@ def test_autotune_leaves_state_unchanged(fx, precision, tmp_path):
     a.step(3, "vay")
     cache = str(tmp_path / "tune.json")
     v, s = a.autotune("vay", trial_steps=16, cache=cache)
-    assert v in range(2, 13) and s in (8, 12, 16, 32)
+    assert v in range(2, 17) and s in (8, 12, 16, 32)
     a.step(20, "vay").sync()
     b = fetdpic.Simulation(w, precision=precision, spai_level=1).load()
     b.step(3, "vay")
