@@ -64,7 +64,12 @@ typedef enum {
     FETDPIC_EWALK = -5,      /* a particle crossed more than max_crossings edges in one step */
     FETDPIC_EOUTSIDE = -6,   /* a loaded particle lies in no triangle */
     FETDPIC_ENONFINITE = -7, /* a momentum or position became NaN/Inf */
-    FETDPIC_ETIMEOUT = -8,   /* a kernel's bounded wait (staged copies) gave up; results of that step are invalid */
+    FETDPIC_ETIMEOUT = -8,   /* a kernel's bounded wait (staged copies, a grid barrier) gave up:
+                                that step is incomplete.  Reporting it discards the current that
+                                step deposited and clears the grid-barrier state; particles and
+                                fields are those of a partial step, so restore them from a
+                                checkpoint (fetdpic_write_particles, fetdpic_write_fields)
+                                before stepping on */
     FETDPIC_ESTATE = -9      /* call not valid in the current state */
 } fetdpic_status;
 
@@ -124,7 +129,8 @@ typedef struct {
     void (*dev_free)(void *ptr, void *user);
     void *alloc_user;
     long long wait_spin_limit; /* polls of each bounded wait inside a kernel (variant 5's staged
-                                copies) before it gives up and reports FETDPIC_ETIMEOUT;
+                                copies, the grid barriers of cooperative launches) before it
+                                gives up and reports FETDPIC_ETIMEOUT;
                                 0 = 2^20; negative = no poll, every such wait gives up at
                                 once (exercises the timeout path) */
     int fuse_field_update;   /* 1 = the Ampere update (C^T [*mu^-1] b - i, then the SPAI

@@ -45,7 +45,8 @@ def _cuda_home(nvcc: str) -> str:
 
 def _sources():
     return [os.path.join(SRC, f) for f in list(CU_SOURCES) + CPP_SOURCES] + \
-        [os.path.join(SRC, "fetdpic_internal.h"), os.path.join(INCLUDE, "fetdpic.h")]
+        [os.path.join(SRC, "fetdpic_internal.h"), os.path.join(SRC, "field_device.cuh"),
+         os.path.join(INCLUDE, "fetdpic.h")]
 
 
 def up_to_date() -> bool:

@@ -59,7 +59,7 @@ struct fetdpic_ctx {
     long long *m_soff = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
     float *m_v32 = nullptr, *r32 = nullptr;
     unsigned *status = nullptr;
-    unsigned *gbar = nullptr;                // grid-barrier state of the fused Ampere launch
+    unsigned *gbar = nullptr;                // grid-barrier state of the fused Ampere launch (GBAR_WORDS)
     std::vector<double> unit_host;           // per instance (q_ref/dt) / scale
     std::vector<double> fixscale;            // per instance fixed-point scale (2^shift in FP64)
     std::vector<double> qunit_host;          // per instance charge of one fixed-point unit: q_ref / scale
@@ -206,6 +206,12 @@ static int take_status(fetdpic_ctx *ctx)
     unsigned st = 0;
     CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (st) CK(cudaMemset(ctx->status, 0, sizeof(unsigned)));
+    // a step that timed out is incomplete: drop the current it deposited, and the counts a grid
+    // barrier that gave up left behind
+    if (st & ST_TIMEOUT) {
+        if (ctx->gbar) CK(cudaMemset(ctx->gbar, 0, sizeof(unsigned) * GBAR_WORDS));
+        if (ctx->ifix) CK(cudaMemset(ctx->ifix, 0, sizeof(unsigned long long) * ctx->E));
+    }
     return map_status(ctx, st);
 }
 
@@ -455,11 +461,13 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         if (P.precision == FETDPIC_FP32) {
             ctx->m_v32 = ctx->alloc<float>(sv32.size());
             ctx->r32 = ctx->alloc<float>(ctx->E);
+            CK(cudaMemset(ctx->r32, 0, sizeof(float) * ctx->E));     // read by the SPAI product
         } else {
             ctx->m_v = ctx->alloc<double>(sv.size());
         }
         ctx->status = ctx->alloc<unsigned>(1);
-        ctx->gbar = ctx->alloc<unsigned>(2);
+        ctx->gbar = ctx->alloc<unsigned>(GBAR_WORDS);
+        if (ctx->gbar) CK(cudaMemset(ctx->gbar, 0, sizeof(unsigned) * GBAR_WORDS));
         if (P.check_interval > 0) {
             ctx->nrp = ctx->alloc<int>(nrp.size());
             ctx->nedge = ctx->alloc<int>(nedge.size());
@@ -867,32 +875,12 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
 {
     long long launches = 0;
     const bool f32 = ctx->p.precision == FETDPIC_FP32;
-    if (timed) mark(ctx, -1);
-    if (f32) {
-        Ext32 x{};
-        if (ctx->ext_on) {
-            x.finst = ctx->face_inst; x.ext = ctx->ext_dev; x.amp = ctx->ext_amp; x.extw = ctx->extw;
-            x.half_over_c = 0.5 / ctx->p.c;
-        }
-        launch_faraday32(ctx->stream, ctx->F, ctx->csta, ctx->cstb, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
-                         (float)(0.5 / (ctx->p.c * ctx->p.c)), x);
-    }
-    else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
-    launches += ctx->F > 0;
-    if (timed) mark(ctx, 0);
     const bool check = ctx->p.check_interval > 0 && ctx->g0 &&
                        ((ctx->steps_done + 1) % ctx->p.check_interval == 0);
-    if (check && !ctx->q_prev_valid) { charge_now(ctx, ctx->q0); launches += 2; }
-    if (ctx->nblocks > 0) {
-        if (f32) launch_particles32(ctx->stream, pusher, args32(ctx));
-        else launch_particles64(ctx->stream, pusher, args64(ctx));
-        ++launches;
-    }
-    if (timed) mark(ctx, 1);
-    if (check) {
-        charge_now(ctx, ctx->q1);
-        launch_dce(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->ifix, ctx->q0, ctx->q1, ctx->chk_out);
-        launches += 3;
+    Ext32 x{};
+    if (f32 && ctx->ext_on) {
+        x.finst = ctx->face_inst; x.ext = ctx->ext_dev; x.amp = ctx->ext_amp; x.extw = ctx->extw;
+        x.half_over_c = 0.5 / ctx->p.c;
     }
     AmpereArgs A{};
     A.E = ctx->E; A.efac = ctx->efac; A.ecoef = ctx->ecoef; A.einst = ctx->einst;
@@ -905,6 +893,31 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     A.e = ctx->e;
     A.fused = ctx->p.fuse_field_update != 0;
     A.gbar = ctx->gbar; A.spin = wait_polls(ctx); A.status = ctx->status;
+    // stage events need each stage to start after the previous one: no early launch when timed
+    A.pdl = !timed;
+    if (timed) mark(ctx, -1);
+    if (f32)
+        launch_faraday32(ctx->stream, ctx->F, ctx->csta, ctx->cstb, ctx->dtinv, ctx->e, ctx->b, ctx->rec32,
+                         (float)(0.5 / (ctx->p.c * ctx->p.c)), x, !timed);
+    else launch_faraday64(ctx->stream, ctx->F, ctx->geo64, ctx->topo, ctx->e, ctx->b, ctx->rec64);
+    launches += ctx->F > 0;
+    if (timed) mark(ctx, 0);
+    if (check && !ctx->q_prev_valid) { charge_now(ctx, ctx->q0); launches += 2; }
+    if (ctx->nblocks > 0) {
+        if (f32) {
+            StepArgs32 a = args32(ctx);
+            a.pdl = !timed;
+            launch_particles32(ctx->stream, pusher, a);
+        }
+        else launch_particles64(ctx->stream, pusher, args64(ctx));
+        ++launches;
+    }
+    if (timed) mark(ctx, 1);
+    if (check) {
+        charge_now(ctx, ctx->q1);
+        launch_dce(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->ifix, ctx->q0, ctx->q1, ctx->chk_out);
+        launches += 3;
+    }
     launch_ampere(ctx->stream, A);
     launches += A.fused ? (ctx->E > 0 || ctx->nfree > 0) : (ctx->E > 0) + (ctx->nfree > 0);
     if (ctx->probe_n > 0) {

@@ -140,6 +140,12 @@ struct Species {
     int cell_off, nf;                       // triangle range of the instance
 };
 
+// Grid-barrier state: a top count, a generation and one count per 16 blocks,
+// each on a 128-byte line of its own; enough for cooperative grids of up to
+// GBAR_MAX_BLOCKS blocks.
+constexpr int GBAR_MAX_BLOCKS = 4096;
+constexpr int GBAR_WORDS = 64 + 32 * (GBAR_MAX_BLOCKS / 16);
+
 enum StatusBits : unsigned {
     ST_WALK = 1u, ST_NONFINITE = 2u, ST_MESH = 4u, ST_TIMEOUT = 8u,
     ST_BADCELL = 16u                        // a written particle named a triangle outside its mesh
@@ -147,6 +153,37 @@ enum StatusBits : unsigned {
 
 // ----------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return immediately.
+
+#ifdef __CUDACC__
+// Programmatic dependent launch: with pdl set, the kernel may be launched
+// while the kernel before it on the stream still runs (its blocks become
+// resident as room frees up), which hides the launch gap between the stages of
+// a step.  Every kernel launched this way starts with pdl_begin(), whose
+// griddepcontrol.wait returns only when the previous kernel has completed and
+// its memory is visible; it then lets the next kernel launch early in turn.
+// Without pdl this is a plain launch (and the wait returns at once).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
 
 struct StepArgs64 {
     const Geo64 *geo; const Topo *topo; const Rec64 *rec;
@@ -172,6 +209,7 @@ struct StepArgs32 {
     const Sp32 *sp; const short *chunk_sp;  // species of each 32-particle chunk
     long long nchunks;
     int variant;                            // particle-kernel variant (min resident blocks per SM)
+    bool pdl;                               // programmatic dependent launch (launch_k)
     float *l0, *l1, *ux, *uy; int *cell;
     unsigned long long *ifix;
     unsigned *status;
@@ -191,7 +229,7 @@ void launch_faraday64(cudaStream_t st, int F, const Geo64 *geo, const Topo *topo
 struct __align__(16) ExtField { double ex, ey, bz, pad; };
 struct Ext32 { const int *finst; const ExtField *ext; const double *amp; const double2 *extw; double half_over_c; };
 void launch_faraday32(cudaStream_t st, int F, const CstA *csta, const CstB *cstb, const double2 *dtinv, const double *e,
-                      double *b, Rec32 *rec, float inv2c2, const Ext32 &x);
+                      double *b, Rec32 *rec, float inv2c2, const Ext32 &x, bool pdl);
 void launch_particles64(cudaStream_t st, int pusher, const StepArgs64 &a);
 void launch_particles32(cudaStream_t st, int pusher, const StepArgs32 &a);
 
@@ -209,9 +247,11 @@ struct AmpereArgs {
     // dt-scaled SPAI in sliced ELL: slice offsets, row -> edge, columns, values (FP64 or FP32)
     const long long *m_soff; const int *m_row; const int *m_ci; const double *m_v; const float *m_v32;
     double *e;
-    // one cooperative launch for both phases (fused = true): its grid barrier's state (zeroed by
-    // the launcher), the polls of its bounded wait, and the status word a wait that gives up sets
+    // one cooperative launch for both phases (fused = true): its grid barrier's state (zero at
+    // creation, left zero by every completed barrier, cleared by the host after a timeout), the
+    // polls of its bounded wait, and the status word a wait that gives up sets
     bool fused;
+    bool pdl;                                 // programmatic dependent launch (two-launch form)
     unsigned *gbar;
     unsigned spin;
     unsigned *status;

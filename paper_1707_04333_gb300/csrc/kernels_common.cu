@@ -6,73 +6,9 @@
 #include <cuda_runtime.h>
 
 #include "fetdpic_internal.h"
+#include "field_device.cuh"
 
 namespace fetdpic {
-
-// Static field-update operands (the SPAI in sliced ELL, per-edge face pairs and
-// coefficients) are read once per step while hundreds of MB of particle state
-// stream through L2 between two reads: they are loaded with an L2 evict-last
-// policy so the streaming state, not they, is what L2 drops.
-__device__ __forceinline__ unsigned long long l2_keep()
-{
-    unsigned long long pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-template <typename T> __device__ __forceinline__ T ld_keep(const T *p, unsigned long long pol);
-template <> __device__ __forceinline__ int ld_keep<int>(const int *p, unsigned long long pol)
-{
-    int v;
-    asm("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
-    return v;
-}
-template <> __device__ __forceinline__ float ld_keep<float>(const float *p, unsigned long long pol)
-{
-    float v;
-    asm("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
-    return v;
-}
-template <> __device__ __forceinline__ double ld_keep<double>(const double *p, unsigned long long pol)
-{
-    double v;
-    asm("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
-    return v;
-}
-template <> __device__ __forceinline__ int2 ld_keep<int2>(const int2 *p, unsigned long long pol)
-{
-    int2 v;
-    asm("ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
-    return v;
-}
-template <> __device__ __forceinline__ double2 ld_keep<double2>(const double2 *p, unsigned long long pol)
-{
-    double2 v;
-    asm("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
-    return v;
-}
-
-// r = C^T [*mu^-1] b^{n+1/2} - i^{n+1/2} on edge e (Eq. (semi.dis.curl.2)),
-// with [*mu^-1] = 1/(mu0 A_f) folded into ecoef = s_f/(mu0 A_f).  The
-// fixed-point current is converted (unit = (q_ref/dt) 2^-shift per
-// instance), kept in j for reading, and cleared for the next step.  The dual
-// flux d += dt r accumulates for the Gauss-law check (d == NULL: checks off);
-// r (FP64) is stored for the FP64 SpMV, r32 for the FP32 one (either NULL).
-__device__ __forceinline__ void curl_h_edge(const AmpereArgs &a, int e, unsigned long long keep)
-{
-    const int2 fa = ld_keep(a.efac + e, keep);
-    const double2 cf = ld_keep(a.ecoef + e, keep);
-    double h = a.b[fa.x] * cf.x;
-    if (fa.y >= 0) h += a.b[fa.y] * cf.y;
-    const int in = ld_keep(a.einst + e, keep);
-    const long long iv = (long long)a.ifix[e];
-    a.ifix[e] = 0ull;
-    const double cur = (double)iv * a.inst_unit[in];
-    const double rv = h - cur;
-    if (a.r) a.r[e] = rv;
-    if (a.r32) a.r32[e] = (float)rv;
-    a.j[e] = cur;
-    if (a.d) a.d[e] += a.inst_dt[in] * rv;
-}
 
 // e_free += (dt M) r for one row: SpMV with the dt-scaled SPAI in sliced ELL
 // (slices of 32 rows, each padded to its longest row and stored column-major,
@@ -98,6 +34,7 @@ __device__ __forceinline__ void spai_row(const AmpereArgs &a, const V *__restric
 
 __global__ void k_curl_h(AmpereArgs a)
 {
+    pdl_begin();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= a.E) return;
     curl_h_edge(a, e, l2_keep());
@@ -106,43 +43,13 @@ __global__ void k_curl_h(AmpereArgs a)
 template <typename V>
 __global__ void __launch_bounds__(256) k_spai_sell(AmpereArgs a)
 {
+    pdl_begin();
     const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.nfree) return;
     if constexpr (sizeof(V) == 4) spai_row<float>(a, a.m_v32, a.r32, row, l2_keep());
     else spai_row<double>(a, a.m_v, a.r, row, l2_keep());
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks resident): the last
-// block to arrive resets the count and advances the generation; the others
-// poll the generation at most `spin` times (sleeping briefly between polls)
-// and give up after that, setting ST_TIMEOUT, so no wait is unbounded.
-// Returns false in every thread of a block that gave up.
-__device__ __forceinline__ bool grid_sync(unsigned *gbar, unsigned spin, unsigned *status)
-{
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned *gen = gbar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        int ok = 1;
-        if (atomicAdd(gbar, 1u) == gridDim.x - 1) {
-            gbar[0] = 0u;
-            __threadfence();
-            atomicAdd(gbar + 1, 1u);
-        } else {
-            unsigned k = 0;
-            while (*gen == g) {
-                if (k++ >= spin) { ok = 0; atomicOr(status, (unsigned)ST_TIMEOUT); break; }
-                if (k > 4096) __nanosleep(32);           // busy first, then back off
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
 
 // Both Ampere phases in one cooperative launch: r on every edge (grid-stride),
 // a grid barrier (the SpMV reads r anywhere), then e += dt M r on every free
@@ -158,7 +65,7 @@ __global__ void __launch_bounds__(FUSED_BLOCK) k_ampere_fused(AmpereArgs a)
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nth = (long long)gridDim.x * blockDim.x;
     for (long long e = tid; e < a.E; e += nth) curl_h_edge(a, (int)e, keep);
-    if (!grid_sync(a.gbar, a.spin, a.status)) return;
+    if (!grid_barrier(a.gbar, a.spin, a.status)) return;
     for (long long row = tid; row < a.nfree; row += nth) {
         if constexpr (sizeof(V) == 4) spai_row<float>(a, a.m_v32, a.r32, row, keep);
         else spai_row<double>(a, a.m_v, a.r, row, keep);
@@ -178,8 +85,9 @@ static void launch_fused(cudaStream_t st, const AmpereArgs &a)
         if (per_sm < 1) per_sm = 1;
     }
     const long long work = std::max<long long>(a.E, a.nfree);
-    const long long grid = std::min<long long>((work + FUSED_BLOCK - 1) / FUSED_BLOCK, (long long)per_sm * sms);
-    cudaMemsetAsync(a.gbar, 0, 2 * sizeof(unsigned), st);
+    const long long grid = std::min<long long>(std::min<long long>((work + FUSED_BLOCK - 1) / FUSED_BLOCK,
+                                                                    (long long)per_sm * sms),
+                                                GBAR_MAX_BLOCKS);
     AmpereArgs arg = a;
     void *params[] = {&arg};
     cudaLaunchCooperativeKernel((const void *)k_ampere_fused<V>, dim3((unsigned)grid), dim3(FUSED_BLOCK), params, 0,
@@ -194,11 +102,11 @@ void launch_ampere(cudaStream_t st, const AmpereArgs &a)
         else launch_fused<double>(st, a);
         return;
     }
-    if (a.E > 0) k_curl_h<<<(a.E + 255) / 256, 256, 0, st>>>(a);
+    if (a.E > 0) launch_k(a.pdl, k_curl_h, dim3((a.E + 255) / 256), dim3(256), st, a);
     if (a.nfree > 0) {
-        const unsigned g = (unsigned)((a.nfree + 255) / 256);
-        if (a.m_v32) k_spai_sell<float><<<g, 256, 0, st>>>(a);
-        else k_spai_sell<double><<<g, 256, 0, st>>>(a);
+        const dim3 g((unsigned)((a.nfree + 255) / 256));
+        if (a.m_v32) launch_k(a.pdl, k_spai_sell<float>, g, dim3(256), st, a);
+        else launch_k(a.pdl, k_spai_sell<double>, g, dim3(256), st, a);
     }
 }
 

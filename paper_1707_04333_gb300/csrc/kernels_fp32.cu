@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "fetdpic_internal.h"
+#include "field_device.cuh"
 
 namespace fetdpic {
 
@@ -22,17 +23,12 @@ namespace fetdpic {
 // as dt/(2c) V_n = (s_{n-1} e_{n-1} G_{n+1} - s_{n+1} e_{n+1} G_{n-1}) / (2c^2)
 // (G = c dt grad l), so that q/m times it is alpha E / c; B_z^n stored as
 // (dt/2) B_z = (dt/2) (b^{n+1/2} + b^{n-1/2}) / (2A).
-template <bool EXT>
-__global__ void __launch_bounds__(256) k_faraday32(int F, const CstA *__restrict__ csta,
-                                                   const CstB *__restrict__ cstb,
-                                                   const double2 *__restrict__ dtinv,
-                                                   const double *__restrict__ e, double *__restrict__ b,
-                                                   Rec32 *__restrict__ rec, float inv2c2, Ext32 x)
+__device__ __forceinline__ void faraday32_tri(int f, const CstA *__restrict__ csta, const CstB *__restrict__ cstb,
+                                              const double2 *__restrict__ dtinv, const double *e, double *b,
+                                              Rec32 *rec, float inv2c2, const Ext32 &x, bool ext)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= F) return;
     const float4 *cp = reinterpret_cast<const float4 *>(csta + f);
-    const float4 c0 = cp[0], c1 = cp[1];
+    const float4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
     const CstB cb = cstb[f];
     // G_2 = -(G_0 + G_1): the barycentric gradients of a triangle sum to zero
     const float G[6] = {c0.x, c0.y, c0.z, c0.w, -(c0.x + c0.z), -(c0.y + c0.w)};
@@ -56,7 +52,7 @@ __global__ void __launch_bounds__(256) k_faraday32(int F, const CstA *__restrict
         r.v[2 * n + 1] = s[nm] * G[2 * np + 1] - s[np] * G[2 * nm + 1];
     }
     double bfield = (bn + bo) * di.y;
-    if (EXT) {
+    if (ext) {
         // a uniform applied E adds the same value to every node coefficient (sum of lambdas = 1)
         const int k = x.finst[f];
         const ExtField X = x.ext[k];
@@ -74,14 +70,26 @@ __global__ void __launch_bounds__(256) k_faraday32(int F, const CstA *__restrict
     rp[1] = make_float4(r.v[4], r.v[5], r.bz, __int_as_float(ew[0]));
 }
 
+template <bool EXT>
+__global__ void __launch_bounds__(256) k_faraday32(int F, const CstA *__restrict__ csta,
+                                                   const CstB *__restrict__ cstb,
+                                                   const double2 *__restrict__ dtinv,
+                                                   const double *__restrict__ e, double *__restrict__ b,
+                                                   Rec32 *__restrict__ rec, float inv2c2, Ext32 x)
+{
+    pdl_begin();
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= F) return;
+    faraday32_tri(f, csta, cstb, dtinv, e, b, rec, inv2c2, x, EXT);
+}
+
 void launch_faraday32(cudaStream_t st, int F, const CstA *csta, const CstB *cstb, const double2 *dtinv,
-                      const double *e, double *b, Rec32 *rec, float inv2c2, const Ext32 &x)
+                      const double *e, double *b, Rec32 *rec, float inv2c2, const Ext32 &x, bool pdl)
 {
     if (F <= 0) return;
-    if (x.ext)
-        k_faraday32<true><<<(F + 255) / 256, 256, 0, st>>>(F, csta, cstb, dtinv, e, b, rec, inv2c2, x);
-    else
-        k_faraday32<false><<<(F + 255) / 256, 256, 0, st>>>(F, csta, cstb, dtinv, e, b, rec, inv2c2, x);
+    const dim3 g((F + 255) / 256);
+    if (x.ext) launch_k(pdl, k_faraday32<true>, g, dim3(256), st, F, csta, cstb, dtinv, e, b, rec, inv2c2, x);
+    else launch_k(pdl, k_faraday32<false>, g, dim3(256), st, F, csta, cstb, dtinv, e, b, rec, inv2c2, x);
 }
 
 // --------------------------------------------------------------- pushers
@@ -610,6 +618,7 @@ __device__ __forceinline__ void drain(const StepArgs32 &a, WalkItem *q, unsigned
 template <int PUSHER, int MINB, int NW>
 __global__ void __launch_bounds__(NW * 32, MINB) k_particles32(StepArgs32 a)
 {
+    pdl_begin();
     __shared__ WalkItem qbuf[NW][P32_QUEUE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WalkItem *q = qbuf[warp];
@@ -743,6 +752,7 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
 template <int PUSHER, int MINB, int NW, bool SEQ, int WT = 0>
 __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
 {
+    pdl_begin();
     __shared__ WalkItem qbuf[NW][P32_QUEUE2];
     __shared__ unsigned wlo[WT > 0 ? 3 * WT : 1];
     __shared__ int whi[WT > 0 ? 3 * WT : 1];
@@ -884,6 +894,7 @@ __device__ __forceinline__ void stage_issue(const StepArgs32 &a, unsigned c, Sta
 template <int PUSHER>
 __global__ void __launch_bounds__(P32_BLOCK, 3) k_particles32_staged(StepArgs32 a)
 {
+    pdl_begin();
     __shared__ WalkItem qbuf[P32_WARPS][P32_QUEUE];
     __shared__ StageBuf sbuf[P32_WARPS][ST_DEPTH];
     __shared__ unsigned long long sbar[P32_WARPS][ST_DEPTH];
@@ -960,7 +971,7 @@ static void launch_p32(cudaStream_t st, const StepArgs32 &a)
     const long long need = (a.nchunks + NW - 1) / NW;
     const long long grid = std::min<long long>(need, (long long)per_sm * sms);
     if (grid <= 0) return;
-    k_particles32<PUSHER, MINB, NW><<<(unsigned)grid, NW * 32, 0, st>>>(a);
+    launch_k(a.pdl, k_particles32<PUSHER, MINB, NW>, dim3((unsigned)grid), dim3(NW * 32), st, a);
 }
 
 template <int PUSHER, int MINB, int NW, bool SEQ = false, int WT = 0>
@@ -978,7 +989,7 @@ static void launch_p32x2(cudaStream_t st, const StepArgs32 &a)
     const long long need = (a.nchunks / 2 + NW - 1) / NW;
     const long long grid = std::min<long long>(need, (long long)per_sm * sms);
     if (grid <= 0) return;
-    k_particles32x2<PUSHER, MINB, NW, SEQ, WT><<<(unsigned)grid, NW * 32, 0, st>>>(a);
+    launch_k(a.pdl, k_particles32x2<PUSHER, MINB, NW, SEQ, WT>, dim3((unsigned)grid), dim3(NW * 32), st, a);
 }
 
 template <int PUSHER>
@@ -996,7 +1007,7 @@ static void launch_p32s(cudaStream_t st, const StepArgs32 &a)
     const long long need = (a.nchunks + P32_WARPS - 1) / P32_WARPS;
     const long long grid = std::min<long long>(need, (long long)per_sm * sms);
     if (grid <= 0) return;
-    k_particles32_staged<PUSHER><<<(unsigned)grid, P32_BLOCK, 0, st>>>(a);
+    launch_k(a.pdl, k_particles32_staged<PUSHER>, dim3((unsigned)grid), dim3(P32_BLOCK), st, a);
 }
 
 template <int PUSHER>
