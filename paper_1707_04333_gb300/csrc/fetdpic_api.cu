@@ -682,8 +682,8 @@ static int finalize(fetdpic_ctx *ctx)
     }
     ctx->P = off;
     ctx->nblocks = off / ctx->block;
-    if (P.record_walk > 0 && off >= (1ll << 31))
-        return ctx->fail(FETDPIC_EINVAL, "record_walk needs fewer than 2^31 particle slots");
+    if (off >= (1ll << 31))      // particle slots and load indices are 32-bit
+        return ctx->fail(FETDPIC_EINVAL, "more than 2^31 - 1 particle slots (species padded to 1024)");
     ctx->hist_n = hist_n;
     const bool f32 = P.precision == FETDPIC_FP32;
     const size_t fb = f32 ? 4 : 8;
@@ -861,7 +861,7 @@ static void do_sort(fetdpic_ctx *ctx)
     for (int k = 0; k < 4; ++k) { s.f[k] = ctx->f[k]; s.f_tmp[k] = ctx->f_tmp[k]; }
     s.fbytes = ctx->p.precision == FETDPIC_FP32 ? 4 : 8;
     s.hist = ctx->hist; s.hoff = ctx->hoff; s.hist_n = ctx->hist_n; s.scan_tmp = ctx->scan_tmp;
-    s.pad_adj_dev = ctx->pad_adj; s.blk_sp = ctx->blk_sp; s.nblocks = ctx->nblocks; s.block = ctx->block;
+    s.pad_adj_dev = ctx->pad_adj;
     s.chunk_sp = ctx->chunk_sp;
     launch_sort(ctx->stream, s);
     std::swap(ctx->cell, ctx->cell_tmp);

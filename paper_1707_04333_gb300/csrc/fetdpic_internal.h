@@ -270,7 +270,6 @@ struct SortArgs {
     long long hist_n;
     int *scan_tmp;                            // scratch for the block sums
     const long long *pad_adj_dev;             // per species storage_off - packed_off
-    const short *blk_sp; long long nblocks; int block;
     const short *chunk_sp;                    // species of each 32-particle chunk
 };
 void launch_sort(cudaStream_t st, const SortArgs &a);

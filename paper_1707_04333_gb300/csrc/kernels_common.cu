@@ -215,17 +215,34 @@ __device__ __forceinline__ WarpRun warp_run(int key, int lane)
     return r;
 }
 
-// Histogram: one integer atomic per run of equal triangle in a warp.
-__global__ void k_hist(const int *__restrict__ cell, const short *__restrict__ blk_sp, const Species *__restrict__ sp,
-                       const int *__restrict__ hoff, int *__restrict__ hist)
+// Histogram: one integer atomic per run of equal triangle in a warp.  Each
+// warp takes HI_UNROLL consecutive 32-particle chunks at a time, their keys
+// loaded before any is used, so several loads per warp are in flight; the grid
+// is one wave, striding over the chunks.
+constexpr int HI_UNROLL = 8;
+
+__global__ void __launch_bounds__(256) k_hist(long long nchunks, const int *__restrict__ cell,
+                                              const short *__restrict__ chunk_sp, const Species *__restrict__ sp,
+                                              const int *__restrict__ hoff, int *__restrict__ hist)
 {
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const int c = cell[p];
-    const int s = blk_sp[blockIdx.x];
-    const int slot = c < 0 ? -1 : hoff[s] + (c - sp[s].cell_off);
-    const WarpRun r = warp_run(slot, lane);
-    if (slot >= 0 && r.head) atomicAdd(hist + slot, r.len);
+    const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c0 = w * HI_UNROLL; c0 < nchunks; c0 += nw * HI_UNROLL) {
+        int cc[HI_UNROLL], sid[HI_UNROLL];
+#pragma unroll
+        for (int k = 0; k < HI_UNROLL; ++k) {
+            const long long ch = c0 + k;
+            cc[k] = -1; sid[k] = 0;
+            if (ch < nchunks) { cc[k] = __ldcs(cell + ch * 32 + lane); sid[k] = chunk_sp[ch]; }
+        }
+#pragma unroll
+        for (int k = 0; k < HI_UNROLL; ++k) {
+            const int slot = cc[k] < 0 ? -1 : hoff[sid[k]] + (cc[k] - sp[sid[k]].cell_off);
+            const WarpRun r = warp_run(slot, lane);
+            if (slot >= 0 && r.head) atomicAdd(hist + slot, r.len);
+        }
+    }
 }
 
 // Scatter through per-triangle cursors.  Each warp handles SC_CHUNKS
@@ -289,7 +306,16 @@ __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *_
 void launch_sort(cudaStream_t st, const SortArgs &a)
 {
     cudaMemsetAsync(a.hist, 0, sizeof(int) * a.hist_n, st);
-    k_hist<<<(unsigned)a.nblocks, a.block, 0, st>>>(a.cell, a.blk_sp, a.sp_dev, a.hoff, a.hist);
+    {
+        static int sms = 0, dev = -1;
+        int d = 0;
+        cudaGetDevice(&d);
+        if (d != dev || sms == 0) { cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d); dev = d; }
+        const long long nch = a.P / 32;
+        const long long need = (nch + 8 * HI_UNROLL - 1) / (8 * HI_UNROLL);    // 8 warps per block
+        const long long grid = std::max<long long>(1, std::min<long long>(need, 8LL * sms));
+        k_hist<<<(unsigned)grid, 256, 0, st>>>(nch, a.cell, a.chunk_sp, a.sp_dev, a.hoff, a.hist);
+    }
     // exclusive scan in place into the cursor array (hist doubles as cursor)
     launch_exclusive_scan(st, a.hist, a.hist, a.hist_n, a.scan_tmp);
     const long long nchunks = a.P / 32;
