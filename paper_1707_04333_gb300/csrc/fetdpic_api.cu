@@ -39,6 +39,11 @@ struct fetdpic_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // a stream of the context's own on which the particle sort runs beside the
+    // Ampere update (both only read what the particle kernel wrote), forked
+    // from and joined back into `stream` by the two events
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
 
     std::vector<HostMesh> mesh;
@@ -111,9 +116,12 @@ struct fetdpic_ctx {
     // reusable device scratch for host <-> device transfers of particle state
     void *xfer = nullptr; size_t xfer_bytes = 0;
 
-    // captured one-step graphs: [pusher][particle-buffer parity][step sorts]
-    cudaGraphExec_t graph[4][2][2] = {};
-    long long graph_launches[4][2][2] = {};
+    // captured one-step graphs: [pusher][particle-buffer parity][step sorts][late hybrid step]
+    cudaGraphExec_t graph[4][2][2][2] = {};
+    long long graph_launches[4][2][2][2] = {};
+    // captured sort cycles (sort_interval steps, the last of which sorts): [pusher][parity at the start]
+    cudaGraphExec_t cycle[4][2] = {};
+    long long cycle_launches[4][2] = {};
     int *cell_a = nullptr;                    // the first particle buffer (parity reference)
 
     std::vector<void *> allocs;
@@ -128,12 +136,17 @@ struct fetdpic_ctx {
     {
         cudaSetDevice(device);
         if (stream) cudaStreamSynchronize(stream);
-        for (auto &a : graph) for (auto &b : a) for (auto &g : b) if (g) cudaGraphExecDestroy(g);
+        for (auto &a : graph) for (auto &b : a) for (auto &c : b) for (auto &g : c) if (g) cudaGraphExecDestroy(g);
+        for (auto &a : cycle) for (auto &g : a) if (g) cudaGraphExecDestroy(g);
         for (void *q : allocs) {
             if (p.dev_free) p.dev_free(q, p.alloc_user);
             else cudaFree(q);
         }
         for (auto &x : ev) cudaEventDestroy(x);
+        if (side) cudaStreamSynchronize(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
 
@@ -237,12 +250,15 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.record_walk < 0) return FETDPIC_EINVAL;
     // untuned FP32 default: two particles per thread in 64-thread blocks (20 warps per SM at 96
     // registers), measured fastest on the benchmark workload
-    if (P.kernel_variant < 0 || P.kernel_variant == 1 || P.kernel_variant > 16) return FETDPIC_EINVAL;
+    if (P.kernel_variant < 0 || P.kernel_variant == 1 || P.kernel_variant > 18) return FETDPIC_EINVAL;
     if (P.kernel_variant == 0) P.kernel_variant = 10;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
     if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
     else { CK(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking)); ctx->own_stream = true; }
+    CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
 
     // ---- host setup per instance
     ctx->mesh.resize(n_inst);
@@ -807,12 +823,24 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
     return a;
 }
 
+// FP32 particle-kernel variant of the coming step.  The hybrids 17 and 18 run
+// variant 12 for the first 6 (17) or 4 (18) steps after a sort, while runs of
+// equal triangle are long, and the deposit-window variant 14 once the particles
+// have drifted; all variants give identical results.
+static int step_variant(const fetdpic_ctx *ctx)
+{
+    const int v = ctx->p.kernel_variant;
+    if (v != 17 && v != 18) return v;
+    const long long since = ctx->p.sort_interval > 0 ? ctx->steps_done % ctx->p.sort_interval : ctx->steps_done;
+    return since < (v == 17 ? 6 : 4) ? 12 : 14;
+}
+
 static StepArgs32 args32(fetdpic_ctx *ctx)
 {
     StepArgs32 a{};
     a.csta = ctx->csta; a.cstb = ctx->cstb; a.rec = ctx->rec32;
     a.sp = ctx->sp32_dev; a.chunk_sp = ctx->chunk_sp; a.nchunks = ctx->P / 32;
-    a.variant = ctx->p.kernel_variant;
+    a.variant = step_variant(ctx);
     a.l0 = (float *)ctx->f[0]; a.l1 = (float *)ctx->f[1]; a.ux = (float *)ctx->f[2]; a.uy = (float *)ctx->f[3];
     a.cell = ctx->cell;
     a.ifix = ctx->ifix; a.status = ctx->status;
@@ -852,7 +880,7 @@ static void collect_events(fetdpic_ctx *ctx)
     ctx->ev_used = 0;
 }
 
-static void do_sort(fetdpic_ctx *ctx)
+static void do_sort(fetdpic_ctx *ctx, cudaStream_t st)
 {
     SortArgs s{};
     s.nsp = (int)ctx->sp.size(); s.sp_dev = ctx->sp_dev; s.sp_host = ctx->sp.data();
@@ -863,7 +891,7 @@ static void do_sort(fetdpic_ctx *ctx)
     s.hist = ctx->hist; s.hoff = ctx->hoff; s.hist_n = ctx->hist_n; s.scan_tmp = ctx->scan_tmp;
     s.pad_adj_dev = ctx->pad_adj;
     s.chunk_sp = ctx->chunk_sp;
-    launch_sort(ctx->stream, s);
+    launch_sort(st, s);
     std::swap(ctx->cell, ctx->cell_tmp);
     std::swap(ctx->id, ctx->id_tmp);
     for (int k = 0; k < 4; ++k) std::swap(ctx->f[k], ctx->f_tmp[k]);
@@ -913,6 +941,18 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
         ++launches;
     }
     if (timed) mark(ctx, 1);
+    // the sort of this step's end reads only the particle state, which the Ampere update
+    // does not touch: without stage events or checks it runs on the side stream meanwhile
+    const bool sorts = ctx->p.sort_interval > 0 && ctx->nblocks > 0 &&
+                       (ctx->steps_done + 1) % ctx->p.sort_interval == 0;
+    const bool side_sort = sorts && !timed && !check;
+    if (side_sort) {
+        cudaEventRecord(ctx->ev_fork, ctx->stream);       // errors surface through cudaGetLastError
+        cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+        do_sort(ctx, ctx->side);
+        launches += 4;
+        cudaEventRecord(ctx->ev_join, ctx->side);
+    }
     if (check) {
         charge_now(ctx, ctx->q1);
         launch_dce(ctx->stream, ctx->N, ctx->nrp, ctx->nedge, ctx->ninst, ctx->ifix, ctx->q0, ctx->q1, ctx->chk_out);
@@ -939,9 +979,11 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
         ctx->q_prev_valid = false;
     }
     ++ctx->steps_done;
-    if (ctx->p.sort_interval > 0 && ctx->nblocks > 0 && ctx->steps_done % ctx->p.sort_interval == 0) {
-        do_sort(ctx);
-        launches += 5;
+    if (side_sort) {
+        cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0);
+    } else if (sorts) {
+        do_sort(ctx, ctx->stream);
+        launches += 4;
         if (timed) mark(ctx, 4);
     }
     return launches;
@@ -956,7 +998,9 @@ static int graph_step(fetdpic_ctx *ctx, int pusher, long long &launches)
     const bool sorts = ctx->p.sort_interval > 0 && ctx->nblocks > 0 &&
                        (ctx->steps_done + 1) % ctx->p.sort_interval == 0;
     const int parity = ctx->cell == ctx->cell_a ? 0 : 1;
-    cudaGraphExec_t &g = ctx->graph[pusher][parity][sorts ? 1 : 0];
+    const int kv = ctx->p.kernel_variant;
+    const int late = ctx->p.precision == FETDPIC_FP32 && (kv == 17 || kv == 18) && step_variant(ctx) == 14 ? 1 : 0;
+    cudaGraphExec_t &g = ctx->graph[pusher][parity][sorts ? 1 : 0][late];
     if (!g) {
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -966,13 +1010,13 @@ static int graph_step(fetdpic_ctx *ctx, int pusher, long long &launches)
         e = cudaGraphInstantiate(&g, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) { g = nullptr; return ctx->cuda_fail(e, "cudaGraphInstantiate"); }
-        ctx->graph_launches[pusher][parity][sorts ? 1 : 0] = n;
+        ctx->graph_launches[pusher][parity][sorts ? 1 : 0][late] = n;
         CK(cudaGraphLaunch(g, ctx->stream));
         launches += n;
         return FETDPIC_OK;
     }
     CK(cudaGraphLaunch(g, ctx->stream));
-    launches += ctx->graph_launches[pusher][parity][sorts ? 1 : 0];
+    launches += ctx->graph_launches[pusher][parity][sorts ? 1 : 0][late];
     // host-side effects of the step the graph replays
     ++ctx->steps_done;
     ctx->q_prev_valid = false;
@@ -981,6 +1025,42 @@ static int graph_step(fetdpic_ctx *ctx, int pusher, long long &launches)
         std::swap(ctx->id, ctx->id_tmp);
         for (int k = 0; k < 4; ++k) std::swap(ctx->f[k], ctx->f_tmp[k]);
     }
+    return FETDPIC_OK;
+}
+
+// A whole sort cycle (sort_interval steps from just after a sort up to and
+// including the next one) through one captured graph: inside it every kernel
+// may launch early behind the previous one (programmatic dependent launch),
+// across step boundaries too, and the cycle is one graph launch.  The graph
+// depends on the pusher and on which particle buffer is current at its start.
+static int cycle_step(fetdpic_ctx *ctx, int pusher, long long &launches)
+{
+    const int parity = ctx->cell == ctx->cell_a ? 0 : 1;
+    const int L = ctx->p.sort_interval;
+    cudaGraphExec_t &g = ctx->cycle[pusher][parity];
+    if (!g) {
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        long long n = 0;
+        for (int k = 0; k < L; ++k) n += enqueue_step(ctx, pusher, false);
+        cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+        if (e != cudaSuccess) return ctx->cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { g = nullptr; return ctx->cuda_fail(e, "cudaGraphInstantiate"); }
+        ctx->cycle_launches[pusher][parity] = n;
+        CK(cudaGraphLaunch(g, ctx->stream));
+        launches += n;
+        return FETDPIC_OK;
+    }
+    CK(cudaGraphLaunch(g, ctx->stream));
+    launches += ctx->cycle_launches[pusher][parity];
+    // host-side effects of the replayed steps: one sort, at the end
+    ctx->steps_done += L;
+    ctx->q_prev_valid = false;
+    std::swap(ctx->cell, ctx->cell_tmp);
+    std::swap(ctx->id, ctx->id_tmp);
+    for (int k = 0; k < 4; ++k) std::swap(ctx->f[k], ctx->f_tmp[k]);
     return FETDPIC_OK;
 }
 
@@ -1001,6 +1081,13 @@ extern "C" int fetdpic_step(fetdpic_ctx *ctx, long long nsteps, int pusher)
     const bool graphs = ctx->p.use_graphs != 0 && !timed && ctx->p.check_interval <= 0;
     for (long long s = 0; s < nsteps; ++s) {
         if (graphs) {
+            const int L = ctx->p.sort_interval;
+            if (L > 1 && ctx->nblocks > 0 && ctx->steps_done % L == 0 && nsteps - s >= L) {
+                rc = cycle_step(ctx, pusher, launches);
+                if (rc) return rc;
+                s += L - 1;
+                continue;
+            }
             rc = graph_step(ctx, pusher, launches);
             if (rc) return rc;
             continue;
@@ -1407,7 +1494,10 @@ extern "C" int fetdpic_read_spai(fetdpic_ctx *ctx, int inst, long long *rowptr, 
 
 static void drop_graphs(fetdpic_ctx *ctx)
 {
-    for (auto &a : ctx->graph) for (auto &b : a) for (auto &g : b) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &a : ctx->graph) for (auto &b : a) for (auto &c : b) for (auto &g : c)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &a : ctx->cycle) for (auto &g : a)
+        if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
 extern "C" int fetdpic_set_wait_limit(fetdpic_ctx *ctx, long long wait_spin_limit)
@@ -1422,7 +1512,7 @@ extern "C" int fetdpic_set_wait_limit(fetdpic_ctx *ctx, long long wait_spin_limi
 extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)
 {
     if (!ctx) return FETDPIC_EINVAL;
-    if (variant < 0 || variant > 16 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
+    if (variant < 0 || variant > 18 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
     ctx->p.kernel_variant = variant == 0 ? 10 : variant;    // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
@@ -1473,7 +1563,7 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     ctx->p.check_interval = 0;
     ctx->probe_n = 0;
     rc = copy_state(true);
-    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 14} : std::vector<int>{3};
+    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 14, 17, 18} : std::vector<int>{3};
     std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 12, 16, 32};
     double best = 1e300;
     int bv = keep_variant, bs = keep_sort;

@@ -27,9 +27,12 @@ __device__ __forceinline__ void faraday32_tri(int f, const CstA *__restrict__ cs
                                               const double2 *__restrict__ dtinv, const double *e, double *b,
                                               Rec32 *rec, float inv2c2, const Ext32 &x, bool ext)
 {
+    // the triangle's constants are static: loaded before the wait for the kernel that writes e
     const float4 *cp = reinterpret_cast<const float4 *>(csta + f);
     const float4 c0 = __ldg(cp), c1 = __ldg(cp + 1);
     const CstB cb = cstb[f];
+    const double2 di = dtinv[f];                    // (dt, 1/(2A))
+    pdl_begin();
     // G_2 = -(G_0 + G_1): the barycentric gradients of a triangle sum to zero
     const float G[6] = {c0.x, c0.y, c0.z, c0.w, -(c0.x + c0.z), -(c0.y + c0.w)};
     const int ew[3] = {cb.ew0, __float_as_int(c1.x), __float_as_int(c1.y)};
@@ -39,7 +42,6 @@ __device__ __forceinline__ void faraday32_tri(int f, const CstA *__restrict__ cs
         const double v = e[ew[m] >> 1];
         se[m] = (ew[m] & 1) ? -v : v;
     }
-    const double2 di = dtinv[f];                    // (dt, 1/(2A))
     const double bo = b[f];
     const double bn = bo - di.x * ((se[0] + se[1]) + se[2]);
     b[f] = bn;
@@ -77,9 +79,8 @@ __global__ void __launch_bounds__(256) k_faraday32(int F, const CstA *__restrict
                                                    const double *__restrict__ e, double *__restrict__ b,
                                                    Rec32 *__restrict__ rec, float inv2c2, Ext32 x)
 {
-    pdl_begin();
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= F) return;
+    if (f >= F) { pdl_begin(); return; }
     faraday32_tri(f, csta, cstb, dtinv, e, b, rec, inv2c2, x, EXT);
 }
 
@@ -752,7 +753,6 @@ __device__ __forceinline__ void process_chunk2(const StepArgs32 &a, unsigned c, 
 template <int PUSHER, int MINB, int NW, bool SEQ, int WT = 0>
 __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
 {
-    pdl_begin();
     __shared__ WalkItem qbuf[NW][P32_QUEUE2];
     __shared__ unsigned wlo[WT > 0 ? 3 * WT : 1];
     __shared__ int whi[WT > 0 ? 3 * WT : 1];
@@ -780,6 +780,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) k_particles32x2(StepArgs32 a)
         dw.nt = tc >= 0 ? WT : 0;
         __syncthreads();
     }
+    // Only the field records come from the kernel this one may overlap (Faraday); the
+    // particle state and the cleared current were written before Faraday started, so the
+    // first state load and the window set-up go ahead of the wait.
+    pdl_begin();
     if (c < cend) {
         bool bad = false;
         for (; c < cend; ++c) {
