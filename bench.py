@@ -316,16 +316,19 @@ TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_particles32_pair200k_traffic
 
 def kernel_label(variant):
     """Name of the FP32 particle kernel a variant launches (0 = the library's default, which takes
-    two particles per thread)."""
+    two particles per thread; 17 and 18 switch from variant 12 to 14 a few steps after a sort)."""
     two = variant == 0 or variant >= 8
+    if variant in (17, 18):
+        return (f"k_particles32x2 (gather+push+walk+deposit, variant {variant}: variant 12 for the first "
+                f"{6 if variant == 17 else 4} steps after a sort, then variant 14)")
     return (f"{'k_particles32x2' if two else 'k_particles32'} (gather+push+walk+deposit, "
             f"variant {variant if variant else 'default'})")
 
 
-def measured_traffic(workload, pbytes):
+def measured_traffic(workload, pbytes, variant=None):
     """DRAM bytes (read + write) of one particle-kernel launch from the committed ncu summary, or
-    None when the summary is for another workload or the kernel's sources changed since the
-    capture (their SHA-256 is stored with the figure)."""
+    None when the summary is for another workload or kernel variant, or the kernel's sources
+    changed since the capture (their SHA-256 is stored with the figure)."""
     import hashlib
     try:
         with open(TRAFFIC_SUMMARY) as f:
@@ -334,6 +337,8 @@ def measured_traffic(workload, pbytes):
         return None, "no ncu summary"
     if t.get("workload_flag") != workload or t.get("bytes_per_launch") != pbytes:
         return None, "ncu summary is for another workload"
+    if variant is not None and t.get("variant") != variant:
+        return None, f"ncu summary is for variant {t.get('variant')}, the run used variant {variant}"
     h = hashlib.sha256()
     for rel in t["sources"]:
         with open(os.path.join(ROOT, rel), "rb") as f:
@@ -488,7 +493,7 @@ def main():
     part_ms = st[1] / max(st[3], 1) if st[3] > 0 else 0.0
     peak, peak_kind = peaks()
     achieved = pbytes / (part_ms / 1e3) / 1e9 if part_ms > 0 else None
-    traffic, traffic_note = measured_traffic(args.workload, pbytes)
+    traffic, traffic_note = measured_traffic(args.workload, pbytes, tuned[0])
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "kernel": kernel_label(tuned[0]), "peak_kind": peak_kind,

@@ -23,6 +23,8 @@ def test_kernel_label_names_the_kernel_each_variant_launches():
     for v in (0, 8, 9, 10, 11, 12):
         assert b.kernel_label(v).startswith("k_particles32x2 ")
     assert "variant default" in b.kernel_label(0) and "variant 11" in b.kernel_label(11)
+    for v in (17, 18):
+        assert b.kernel_label(v).startswith("k_particles32x2 ") and "variant 14" in b.kernel_label(v)
 
 
 def test_traffic_reported_only_for_the_measured_sources(tmp_path):
@@ -38,6 +40,8 @@ def test_traffic_reported_only_for_the_measured_sources(tmp_path):
     assert b.measured_traffic("pair", 321564800.0)[0] == 289021184.0
     assert b.measured_traffic("beam", 321564800.0)[0] is None            # another workload
     assert b.measured_traffic("pair", 1.0)[0] is None                    # another size
+    assert b.measured_traffic("pair", 321564800.0, 11)[0] == 289021184.0
+    assert b.measured_traffic("pair", 321564800.0, 17)[0] is None        # another variant
     src.write_text("// kernel v2\n")
     t, note = b.measured_traffic("pair", 321564800.0)
     assert t is None and "changed" in note
