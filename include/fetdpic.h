@@ -199,9 +199,11 @@ int fetdpic_load_particles(fetdpic_ctx *ctx, int inst, double q, double m, long 
  * page-locked memory) and converted there, asynchronously on the stream: the
  * host buffers must stay valid until the next fetdpic_sync or read, and a
  * triangle index outside the instance's mesh is found on the device (that
- * particle is dropped) and reported as FETDPIC_EINVAL by the next
- * fetdpic_sync or fetdpic_read.  Used for checkpoint/restart and for
- * end-to-end runs that stream the particle state from the host. */
+ * particle is dropped: it no longer moves, deposits or counts, the other
+ * particles keep their species, and reads return it as missing) and reported
+ * as FETDPIC_EINVAL by the next fetdpic_sync or fetdpic_read.  Used for
+ * checkpoint/restart and for end-to-end runs that stream the particle state
+ * from the host. */
 int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const double *x, const double *u, const int *cell);
 
 /* Overwrite the fields of instance `inst`: e [n_edges] (e^n, PEC entries are
@@ -228,7 +230,9 @@ int fetdpic_sync(fetdpic_ctx *ctx);
  * e^n, b [n_tri] = b^{n-1/2} (the latest face DoFs), j [n_edges] = i^{n-1/2}
  * of the last step (Eq. (I.assign)).  Then species `species` (ignored
  * if x, u and cell are all NULL): x [n][2], u [n][2], cell [n], in load
- * order.  FP32 mode converts barycentric positions to x = sum_k l_k r_k. */
+ * order.  FP32 mode converts barycentric positions to x = sum_k l_k r_k.  A
+ * particle dropped by fetdpic_write_particles reads NaN position and
+ * momentum and triangle -1. */
 int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
                  int species, double *x, double *u, int *cell);
 

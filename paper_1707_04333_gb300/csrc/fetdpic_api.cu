@@ -93,7 +93,6 @@ struct fetdpic_ctx {
     int *tri_i2c = nullptr;                  // [stored global index] -> caller's instance-local index
     bool ext_on = false;                     // FP32: fold applied fields into the field record
     int *hist = nullptr, *hoff = nullptr, *scan_tmp = nullptr; long long hist_n = 0;
-    long long *pad_adj = nullptr;
     int *rec_cnt = nullptr, *rec = nullptr;
 
     long long steps_done = 0;
@@ -664,8 +663,7 @@ static int finalize(fetdpic_ctx *ctx)
         ctx->qunit_host[k] = qr / ctx->fixscale[k];
     }
     ctx->sp.resize(ns);
-    long long off = 0, packed = 0, hist_n = 0;
-    std::vector<long long> pad_adj(ns);
+    long long off = 0, hist_n = 0;
     std::vector<int> hoff(ns);
     for (int s = 0; s < ns; ++s) {
         const StagedSpecies &S = ctx->staged[s];
@@ -690,11 +688,9 @@ static int finalize(fetdpic_ctx *ctx)
         D.off = off;
         D.cell_off = ctx->cell_off[S.inst];
         D.nf = ctx->mesh[S.inst].nf;
-        pad_adj[s] = off - packed;
         hoff[s] = (int)hist_n;
-        hist_n += D.nf;
+        hist_n += D.nf + 1;                  // the species' triangles, then its padding bin
         off += D.cap;
-        packed += D.n;
     }
     ctx->P = off;
     ctx->nblocks = off / ctx->block;
@@ -730,7 +726,6 @@ static int finalize(fetdpic_ctx *ctx)
         ctx->hist = ctx->alloc<int>(std::max<long long>(hist_n, 1));
         ctx->hoff = ctx->alloc<int>(std::max(ns, 1));
         ctx->scan_tmp = ctx->alloc<int>(scan_tmp_ints(std::max<long long>(hist_n, 1)));
-        ctx->pad_adj = ctx->alloc<long long>(std::max(ns, 1));
         if (P.record_walk > 0) {
             ctx->rec_cnt = ctx->alloc<int>(ctx->P);
             ctx->rec = ctx->alloc<int>((size_t)ctx->P * P.record_walk);
@@ -739,7 +734,7 @@ static int finalize(fetdpic_ctx *ctx)
         return FETDPIC_ENOMEM;
     }
     // host images
-    std::vector<int> cell(ctx->P, -1), id(ctx->P, 0);
+    std::vector<int> cell(ctx->P, -1), id(ctx->P, -1);       // padding: no triangle, no load index
     std::vector<char> fh[4];
     for (int k = 0; k < 4; ++k) fh[k].assign(fb * ctx->P, 0);
     std::vector<short> blk(ctx->nblocks);
@@ -785,7 +780,6 @@ static int finalize(fetdpic_ctx *ctx)
     rc = rc ? rc : upload(ctx, ctx->blk_sp, blk.data(), blk.size());
     rc = rc ? rc : upload(ctx, ctx->chunk_sp, chk.data(), chk.size());
     rc = rc ? rc : upload(ctx, ctx->hoff, hoff.data(), hoff.size());
-    rc = rc ? rc : upload(ctx, ctx->pad_adj, pad_adj.data(), pad_adj.size());
     rc = rc ? rc : upload(ctx, ctx->inst_unit, ctx->unit_host.data(), ctx->unit_host.size());
     if (ctx->qunit) {
         rc = rc ? rc : upload(ctx, ctx->qunit, ctx->qunit_host.data(), ctx->qunit_host.size());
@@ -889,7 +883,6 @@ static void do_sort(fetdpic_ctx *ctx, cudaStream_t st)
     for (int k = 0; k < 4; ++k) { s.f[k] = ctx->f[k]; s.f_tmp[k] = ctx->f_tmp[k]; }
     s.fbytes = ctx->p.precision == FETDPIC_FP32 ? 4 : 8;
     s.hist = ctx->hist; s.hoff = ctx->hoff; s.hist_n = ctx->hist_n; s.scan_tmp = ctx->scan_tmp;
-    s.pad_adj_dev = ctx->pad_adj;
     s.chunk_sp = ctx->chunk_sp;
     launch_sort(st, s);
     std::swap(ctx->cell, ctx->cell_tmp);
@@ -1156,7 +1149,7 @@ extern "C" int fetdpic_write_particles(fetdpic_ctx *ctx, int species, const doub
     CK(cudaMemcpyAsync(st, x, bx, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(st + bx, u, bx, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(st + 2 * bx, cl, bc, cudaMemcpyHostToDevice, ctx->stream));
-    launch_ingest(ctx->stream, D.n, D.off, D.cell_off, M.nf, ctx->p.precision == FETDPIC_FP32,
+    launch_ingest(ctx->stream, D.n, D.cap, D.off, D.cell_off, M.nf, ctx->p.precision == FETDPIC_FP32,
                   (const double *)st, (const double *)(st + bx), (const int *)(st + 2 * bx), ctx->tri_c2i, ctx->geo64,
                   1.0 / ctx->p.c, ctx->cell, ctx->id, ctx->f[0], ctx->f[1], ctx->f[2], ctx->f[3], ctx->status);
     CK(cudaGetLastError());
@@ -1273,11 +1266,11 @@ extern "C" int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, do
             double *ox = (double *)st, *ou = (double *)(st + bx);
             int *oc = (int *)(st + 2 * bx);
             if (ctx->p.precision == FETDPIC_FP32)
-                launch_unsort32(ctx->stream, ctx->P, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
+                launch_unsort32(ctx->stream, D.n, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
                                 (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap,
                                 ctx->tri_i2c, ox, ou, oc);
             else
-                launch_unsort64(ctx->stream, ctx->P, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
+                launch_unsort64(ctx->stream, D.n, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
                                 (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, ctx->tri_i2c, ox, ou, oc);
             CK(cudaGetLastError());
             if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1712,11 +1705,11 @@ extern "C" int fetdpic_read_particles_static(fetdpic_ctx *ctx, int species, doub
     double *ox = (double *)st, *ou = (double *)(st + bx);
     int *oc = (int *)(st + 2 * bx);
     if (ctx->p.precision == FETDPIC_FP32)
-        launch_unsort32(ctx->stream, ctx->P, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
+        launch_unsort32(ctx->stream, D.n, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
                         (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap, ctx->tri_i2c,
                         ox, ou, oc);
     else
-        launch_unsort64(ctx->stream, ctx->P, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
+        launch_unsort64(ctx->stream, D.n, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
                         (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, ctx->tri_i2c, ox, ou, oc);
     CK(cudaGetLastError());
     if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->stream));

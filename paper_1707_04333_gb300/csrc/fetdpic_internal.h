@@ -265,11 +265,10 @@ struct SortArgs {
     int *cell; int *cell_tmp;
     int *id; int *id_tmp;
     void *f[4]; void *f_tmp[4]; int fbytes;   // four payload arrays of fbytes each
-    int *hist;                                // sum over species of nf (+1)
+    int *hist;                                // sum over species of (nf + 1): triangles, padding
     int *hoff;                                // per species offset into hist
     long long hist_n;
     int *scan_tmp;                            // scratch for the block sums
-    const long long *pad_adj_dev;             // per species storage_off - packed_off
     const short *chunk_sp;                    // species of each 32-particle chunk
 };
 void launch_sort(cudaStream_t st, const SortArgs &a);
@@ -298,17 +297,21 @@ void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n
 
 // Host-layout particle state into a species range (FP32: barycentrics, u/c).
 // cell: the caller's instance-local triangle indices; c2i maps (cell_off +
-// caller index) to the internal instance-local index.
-void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, int nf, bool fp32, const double *x,
-                   const double *u, const int *cell, const int *c2i, const Geo64 *geo, double inv_c, int *cell_o,
-                   int *id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status);
+// caller index) to the internal instance-local index.  Slots [n, cap) of the
+// range become padding (triangle -1, load index -1).
+void launch_ingest(cudaStream_t st, long long n, long long cap, long long off, int cell_off, int nf, bool fp32,
+                   const double *x, const double *u, const int *cell, const int *c2i, const Geo64 *geo,
+                   double inv_c, int *cell_o, int *id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status);
 
-// Particle state to load order (FP32 converts barycentrics to coordinates);
-// i2c maps an internal global triangle to the caller's instance-local index.
-void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
+// Particle state of a species range [off, off + cap) to load order (FP32
+// converts barycentrics to coordinates); i2c maps an internal global triangle
+// to the caller's instance-local index.  A slot with triangle -1 and a load
+// index in [0, n) is a particle dropped by a write: its entry gets NaN
+// position and momentum and triangle -1.
+void launch_unsort64(cudaStream_t st, long long n, const int *cell, const int *id, const double *x,
                      const double *y, const double *ux, const double *uy, long long off, long long cap,
                      const int *i2c, double *ox, double *ou, int *oc);
-void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
+void launch_unsort32(cudaStream_t st, long long n, const int *cell, const int *id, const float *l0,
                      const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
                      long long off, long long cap, const int *i2c, double *ox, double *ou, int *oc);
 

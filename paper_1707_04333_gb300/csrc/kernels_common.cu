@@ -222,7 +222,12 @@ void launch_exclusive_scan(cudaStream_t st, const int *in, int *out, long long n
 
 // ------------------------------------------------------------------- sort
 // Counting sort by triangle within each species range: histogram (integer
-// atomics), exclusive scan, scatter through per-triangle cursors.  The order
+// atomics), exclusive scan, scatter through per-triangle cursors.  The bins of
+// species s are its triangles, then one bin for its padding slots (and the
+// slots of particles dropped by a write), so the bins of a species count its
+// whole storage range: the scan gives storage slots directly, every slot of
+// the output is written once, and a species whose live count fell keeps its
+// range.  The order
 // of particles inside one triangle depends on atomic order; nothing computed
 // depends on it (the deposit is integer, reads go through the id array).
 
@@ -246,6 +251,12 @@ __device__ __forceinline__ WarpRun warp_run(int key, int lane)
     return r;
 }
 
+// Bin of a slot of a species: its triangle, or the padding bin after them.
+__device__ __forceinline__ int sort_bin(int c, int hoff, const Species &s)
+{
+    return c < 0 ? hoff + s.nf : hoff + (c - s.cell_off);
+}
+
 // Histogram: one integer atomic per run of equal triangle in a warp.  Each
 // warp takes HI_UNROLL consecutive 32-particle chunks at a time, their keys
 // loaded before any is used, so several loads per warp are in flight; the grid
@@ -264,12 +275,12 @@ __global__ void __launch_bounds__(256) k_hist(long long nchunks, const int *__re
 #pragma unroll
         for (int k = 0; k < HI_UNROLL; ++k) {
             const long long ch = c0 + k;
-            cc[k] = -1; sid[k] = 0;
+            cc[k] = -1; sid[k] = -1;
             if (ch < nchunks) { cc[k] = __ldcs(cell + ch * 32 + lane); sid[k] = chunk_sp[ch]; }
         }
 #pragma unroll
         for (int k = 0; k < HI_UNROLL; ++k) {
-            const int slot = cc[k] < 0 ? -1 : hoff[sid[k]] + (cc[k] - sp[sid[k]].cell_off);
+            const int slot = sid[k] < 0 ? -1 : sort_bin(cc[k], hoff[sid[k]], sp[sid[k]]);
             const WarpRun r = warp_run(slot, lane);
             if (slot >= 0 && r.head) atomicAdd(hist + slot, r.len);
         }
@@ -285,7 +296,7 @@ template <int FB>
 __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *__restrict__ cell,
                                                  const int *__restrict__ id, const short *__restrict__ chunk_sp,
                                                  const Species *__restrict__ sp, const int *__restrict__ hoff,
-                                                 int *__restrict__ cursor, const long long *__restrict__ pad_adj,
+                                                 int *__restrict__ cursor,
                                                  const void *f0, const void *f1, const void *f2, const void *f3,
                                                  int *__restrict__ cell_o, int *__restrict__ id_o,
                                                  void *g0, void *g1, void *g2, void *g3)
@@ -302,7 +313,7 @@ __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *_
 #pragma unroll
     for (int k = 0; k < SC_CHUNKS; ++k) {
         const long long ch = c0 + k;
-        cc[k] = -1; sid[k] = 0;
+        cc[k] = -1; sid[k] = -1;
         if (ch < nchunks) {
             const long long p = ch * 32 + lane;
             cc[k] = cell[p]; sid[k] = chunk_sp[ch];
@@ -313,7 +324,7 @@ __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *_
     }
 #pragma unroll
     for (int k = 0; k < SC_CHUNKS; ++k) {
-        slot[k] = cc[k] < 0 ? -1 : hoff[sid[k]] + (cc[k] - sp[sid[k]].cell_off);
+        slot[k] = sid[k] < 0 ? -1 : sort_bin(cc[k], hoff[sid[k]], sp[sid[k]]);
         peers[k] = __match_any_sync(0xffffffffu, slot[k]);
         rank[k] = __popc(peers[k] & ((1u << lane) - 1u));
         base[k] = 0;
@@ -324,7 +335,7 @@ __global__ void __launch_bounds__(256) k_scatter(long long nchunks, const int *_
         const int leader = __ffs(peers[k]) - 1;
         const int b = __shfl_sync(0xffffffffu, base[k], leader);
         if (slot[k] < 0) continue;
-        const long long q = (long long)(b + rank[k]) + pad_adj[sid[k]];
+        const long long q = (long long)(b + rank[k]);
         cell_o[q] = cc[k];
         id_o[q] = idv[k];
         ((T *)g0)[q] = v0[k];
@@ -359,11 +370,11 @@ void launch_sort(cudaStream_t st, const SortArgs &a)
     const long long warps = (nchunks + SC_CHUNKS - 1) / SC_CHUNKS;
     const unsigned grid = (unsigned)((warps * 32 + 255) / 256);
     if (a.fbytes == 8)
-        k_scatter<8><<<grid, 256, 0, st>>>(nchunks, a.cell, a.id, a.chunk_sp, a.sp_dev, a.hoff, a.hist, a.pad_adj_dev,
+        k_scatter<8><<<grid, 256, 0, st>>>(nchunks, a.cell, a.id, a.chunk_sp, a.sp_dev, a.hoff, a.hist,
                                            a.f[0], a.f[1], a.f[2], a.f[3], a.cell_tmp, a.id_tmp, a.f_tmp[0],
                                            a.f_tmp[1], a.f_tmp[2], a.f_tmp[3]);
     else
-        k_scatter<4><<<grid, 256, 0, st>>>(nchunks, a.cell, a.id, a.chunk_sp, a.sp_dev, a.hoff, a.hist, a.pad_adj_dev,
+        k_scatter<4><<<grid, 256, 0, st>>>(nchunks, a.cell, a.id, a.chunk_sp, a.sp_dev, a.hoff, a.hist,
                                            a.f[0], a.f[1], a.f[2], a.f[3], a.cell_tmp, a.id_tmp, a.f_tmp[0],
                                            a.f_tmp[1], a.f_tmp[2], a.f_tmp[3]);
 }
@@ -375,14 +386,19 @@ void launch_sort(cudaStream_t st, const SortArgs &a)
 // barycentric coordinates of x in its triangle and u/c.
 // An instance-local triangle outside [0, nf) is never used as an address: the
 // particle becomes padding and ST_BADCELL reports it at the next sync.
-__global__ void k_ingest(long long n, long long off, int cell_off, int nf, int fp32, const double *__restrict__ x,
+__global__ void k_ingest(long long n, long long cap, long long off, int cell_off, int nf, int fp32, const double *__restrict__ x,
                          const double *__restrict__ u, const int *__restrict__ cell, const int *__restrict__ c2i,
                          const Geo64 *__restrict__ geo, double inv_c, int *__restrict__ cell_o,
                          int *__restrict__ id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+    if (k >= cap) return;
     const long long p = off + k;
+    if (k >= n) {                          // the species' padding: no particle, no load index
+        cell_o[p] = -1;
+        id_o[p] = -1;
+        return;
+    }
     const int cl = cell[k];
     if (cl < 0 || cl >= nf) {
         cell_o[p] = -1;
@@ -410,16 +426,16 @@ __global__ void k_ingest(long long n, long long off, int cell_off, int nf, int f
     }
 }
 
-void launch_ingest(cudaStream_t st, long long n, long long off, int cell_off, int nf, bool fp32, const double *x,
-                   const double *u, const int *cell, const int *c2i, const Geo64 *geo, double inv_c, int *cell_o,
-                   int *id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status)
+void launch_ingest(cudaStream_t st, long long n, long long cap, long long off, int cell_off, int nf, bool fp32,
+                   const double *x, const double *u, const int *cell, const int *c2i, const Geo64 *geo,
+                   double inv_c, int *cell_o, int *id_o, void *f0, void *f1, void *f2, void *f3, unsigned *status)
 {
-    if (n <= 0) return;
-    k_ingest<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, cell_off, nf, fp32 ? 1 : 0, x, u, cell, c2i, geo,
-                                                          inv_c, cell_o, id_o, f0, f1, f2, f3, status);
+    if (cap <= 0) return;
+    k_ingest<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(n, cap, off, cell_off, nf, fp32 ? 1 : 0, x, u, cell, c2i,
+                                                            geo, inv_c, cell_o, id_o, f0, f1, f2, f3, status);
 }
 
-__global__ void k_unsort64(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,
+__global__ void k_unsort64(long long off, long long cap, long long n, const int *__restrict__ cell, const int *__restrict__ id,
                            const double *__restrict__ x, const double *__restrict__ y,
                            const double *__restrict__ ux, const double *__restrict__ uy, const int *__restrict__ i2c,
                            double *__restrict__ ox, double *__restrict__ ou, int *__restrict__ oc)
@@ -428,14 +444,22 @@ __global__ void k_unsort64(long long off, long long cap, const int *__restrict__
     if (k >= cap) return;
     const long long p = off + k;
     const int c = cell[p];
-    if (c < 0) return;
     const long long i = id[p];
+    if (c < 0) {
+        // a particle dropped by a write keeps its load index: it reads NaN and triangle -1
+        if (i >= 0 && i < n) {
+            if (ox) { ox[2 * i] = __longlong_as_double(-1ll); ox[2 * i + 1] = __longlong_as_double(-1ll); }
+            if (ou) { ou[2 * i] = __longlong_as_double(-1ll); ou[2 * i + 1] = __longlong_as_double(-1ll); }
+            if (oc) oc[i] = -1;
+        }
+        return;
+    }
     if (ox) { ox[2 * i] = x[p]; ox[2 * i + 1] = y[p]; }
     if (ou) { ou[2 * i] = ux[p]; ou[2 * i + 1] = uy[p]; }
     if (oc) oc[i] = i2c[c];
 }
 
-__global__ void k_unsort32(long long off, long long cap, const int *__restrict__ cell, const int *__restrict__ id,
+__global__ void k_unsort32(long long off, long long cap, long long n, const int *__restrict__ cell, const int *__restrict__ id,
                            const float *__restrict__ l0, const float *__restrict__ l1,
                            const float *__restrict__ ux, const float *__restrict__ uy,
                            const Geo64 *__restrict__ geo, double c, const int *__restrict__ i2c,
@@ -445,8 +469,16 @@ __global__ void k_unsort32(long long off, long long cap, const int *__restrict__
     if (k >= cap) return;
     const long long p = off + k;
     const int f = cell[p];
-    if (f < 0) return;
     const long long i = id[p];
+    if (f < 0) {
+        // a particle dropped by a write keeps its load index: it reads NaN and triangle -1
+        if (i >= 0 && i < n) {
+            if (ox) { ox[2 * i] = __longlong_as_double(-1ll); ox[2 * i + 1] = __longlong_as_double(-1ll); }
+            if (ou) { ou[2 * i] = __longlong_as_double(-1ll); ou[2 * i + 1] = __longlong_as_double(-1ll); }
+            if (oc) oc[i] = -1;
+        }
+        return;
+    }
     if (ox) {
         const double a = l0[p], b = l1[p];
         const double cc = 1.0 - a - b;
@@ -458,22 +490,20 @@ __global__ void k_unsort32(long long off, long long cap, const int *__restrict__
     if (oc) oc[i] = i2c[f];
 }
 
-void launch_unsort64(cudaStream_t st, long long P, const int *cell, const int *id, const double *x,
+void launch_unsort64(cudaStream_t st, long long n, const int *cell, const int *id, const double *x,
                      const double *y, const double *ux, const double *uy, long long off, long long cap,
                      const int *i2c, double *ox, double *ou, int *oc)
 {
-    (void)P;
     if (cap <= 0) return;
-    k_unsort64<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, x, y, ux, uy, i2c, ox, ou, oc);
+    k_unsort64<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, n, cell, id, x, y, ux, uy, i2c, ox, ou, oc);
 }
 
-void launch_unsort32(cudaStream_t st, long long P, const int *cell, const int *id, const float *l0,
+void launch_unsort32(cudaStream_t st, long long n, const int *cell, const int *id, const float *l0,
                      const float *l1, const float *ux, const float *uy, const Geo64 *geo, double c,
                      long long off, long long cap, const int *i2c, double *ox, double *ou, int *oc)
 {
-    (void)P;
     if (cap <= 0) return;
-    k_unsort32<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, cell, id, l0, l1, ux, uy, geo, c, i2c,
+    k_unsort32<<<(unsigned)((cap + 255) / 256), 256, 0, st>>>(off, cap, n, cell, id, l0, l1, ux, uy, geo, c, i2c,
                                                               ox, ou, oc);
 }
 

@@ -301,3 +301,49 @@ def test_fused_field_update_equals_two_launches(fx, precision):
     for a, b in zip(out[0], out[1]):
         for k in a:
             assert np.array_equal(a[k], b[k]), k
+
+
+def _read_nan_filled(fetdpic, h, sid, n):
+    """fetdpic_read of one species into NaN / -7 filled host buffers, so that a particle the
+    library does not return is seen as such."""
+    x = np.full((n, 2), np.nan)
+    u = np.full((n, 2), np.nan)
+    c = np.full(n, -7, np.int32)
+    fetdpic._check(h, fetdpic.lib().fetdpic_read(h, 0, None, None, None, sid, fetdpic._ptr(x), fetdpic._ptr(u),
+                                                 fetdpic._ptr(c)))
+    return x, u, c
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dropped_particle_changes_no_other_slot(fx, precision):
+    """A particle that fetdpic_write_particles drops (a triangle outside the mesh) is gone for good,
+    and nothing else changes: the sorts that follow keep every species in its own storage range
+    (the next species is not shifted into the slot the drop freed) and leave no earlier content of
+    the other particle buffer behind as a stale copy.  Checked over three sorts by the particles
+    read back (exactly the dropped one missing) and by the total nodal charge, which equals the sum
+    of Q over the live particles (the barycentric weights of a particle sum to 1, Eq.
+    (scatter.charge.assign))."""
+    fetdpic, oracle = fx
+    w = inputs.pair_plasma(16, 6, kT=0.2, wc_over_wp=0.5, seed=31, pusher="vay")
+    sim = fetdpic.Simulation(w, precision=precision, spai_level=1, sort_interval=3).load()
+    sim.step(4, "vay").sync()                        # one sort: both particle buffers hold particles
+    n0, n1 = (len(s.x) for s in w.species)
+    g = sim.read_species(0)
+    cells = g["cell"].copy()
+    cells[5] = len(w.mesh.triangles) + 5
+    fetdpic.fetdpic_write_particles(sim.h, 0, g["x"], g["u"], cells)
+    with pytest.raises(fetdpic.FetdpicError) as ei:
+        fetdpic.fetdpic_sync(sim.h)
+    assert ei.value.code == fetdpic.EINVAL
+    sim.step(9, "vay").sync()                        # three more sorts
+    x0, u0, c0 = _read_nan_filled(fetdpic, sim.h, 0, n0)
+    x1, u1, c1 = _read_nan_filled(fetdpic, sim.h, 1, n1)
+    missing0 = np.nonzero(c0 < 0)[0]
+    assert list(missing0) == [5] and np.isnan(x0[5]).all()
+    assert (c1 >= 0).all() and np.isfinite(x1).all() and np.isfinite(u1).all()
+    q, quantum = fetdpic.fetdpic_read_charge(sim.h)
+    s0, s1 = w.species
+    expect = s0.q * (n0 - 1) + s1.q * n1
+    scale = abs(s0.q) * n0 + abs(s1.q) * n1
+    assert abs(q.sum() - expect) <= 1e-9 * scale + 3 * (n0 + n1) * quantum, (q.sum(), expect, s0.q)
+    sim.close()
