@@ -323,14 +323,12 @@ __device__ __forceinline__ T sel3(const T *a, int k)
 // walk: its slot, starting triangle and barycentrics, pushed momentum and
 // velocity (units of c).
 struct __align__(16) WalkItem {
-    unsigned p;                  // particle slot
+    unsigned p;                  // particle slot (its chunk gives the species)
     int f;                       // starting triangle
-    int sp;                      // species
-    float pad;
-    float l0, l1, l2, pad2;      // barycentrics at the start of the step
+    float l0, l1;                // barycentrics at the start of the step (l2 = 1 - l0 - l1)
     float ux, uy, vx, vy;
 };
-static_assert(sizeof(WalkItem) == 48, "WalkItem layout");
+static_assert(sizeof(WalkItem) == 32, "WalkItem layout");
 
 // 32 bytes (32-byte aligned) in one 256-bit load: one L1 wavefront per distinct
 // line, where two 128-bit loads of the same bytes take two.
@@ -352,14 +350,14 @@ __device__ __forceinline__ void ld_v8(const void *p, float4 &x, float4 &y)
 // 256-bit load is half of what two 128-bit loads of the same bytes take.
 __device__ __forceinline__ void walk_particle(const StepArgs32 &a, const WalkItem it)
 {
-    const Sp32 *spp = a.sp + it.sp;
+    const Sp32 *spp = a.sp + __ldg(a.chunk_sp + (it.p >> 5));
     const float wfix = __ldg(&spp->wfix);
     const int edge_off = __ldg(&spp->edge_off);
     const unsigned p = it.p;
     const long long rp = a.rec_cap > 0 ? (long long)__ldg(&spp->off) + a.id[p] : 0;   // walk record slot
     int f = it.f, ncross = 0, min = -1;
     bool reflected = false;
-    float lin[3] = {it.l0, it.l1, it.l2};
+    float lin[3] = {it.l0, it.l1, 1.f - it.l0 - it.l1};
     float tin = 0.f, ux = it.ux, uy = it.uy, vx = it.vx, vy = it.vy;
     float lfin[3];
     long long carry = 0;                          // current on the entry edge, not yet deposited
@@ -515,8 +513,9 @@ __device__ __forceinline__ POne one_particle(float kappa, float wfix, int f, flo
 __device__ __forceinline__ WalkItem walk_item(unsigned p, int f, int sp, float l0, float l1, const POne &o)
 {
     WalkItem it;
-    it.p = p; it.f = f; it.sp = sp; it.pad = 0.f;
-    it.l0 = l0; it.l1 = l1; it.l2 = 1.f - l0 - l1; it.pad2 = 0.f;
+    (void)sp;
+    it.p = p; it.f = f;
+    it.l0 = l0; it.l1 = l1;
     it.ux = o.ux; it.uy = o.uy; it.vx = o.vx; it.vy = o.vy;
     return it;
 }
