@@ -316,11 +316,13 @@ TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_particles32_pair200k_traffic
 
 def kernel_label(variant):
     """Name of the FP32 particle kernel a variant launches (0 = the library's default, which takes
-    two particles per thread; 17 and 18 switch from variant 12 to 14 a few steps after a sort)."""
+    two particles per thread; the hybrids 17, 18, 21 and 22 switch kernels a few steps after a sort)."""
     two = variant == 0 or variant >= 8
-    if variant in (17, 18):
-        return (f"k_particles32x2 (gather+push+walk+deposit, variant {variant}: variant 12 for the first "
-                f"{6 if variant == 17 else 4} steps after a sort, then variant 14)")
+    hybrids = {17: (12, 6, 14), 18: (12, 4, 14), 21: (19, 6, 14), 22: (19, 6, 20)}
+    if variant in hybrids:
+        early, steps, late = hybrids[variant]
+        return (f"k_particles32x2 (gather+push+walk+deposit, variant {variant}: variant {early} for the first "
+                f"{steps} steps after a sort, then variant {late})")
     return (f"{'k_particles32x2' if two else 'k_particles32'} (gather+push+walk+deposit, "
             f"variant {variant if variant else 'default'})")
 

@@ -121,10 +121,13 @@ typedef struct {
                                 triangles near the block's particles summed there and added to
                                 the global current once per block): 13 and 14 = variant 10 with
                                 320- and 256-triangle windows, 15 = variant 12 with 192, 16 =
-                                variant 9 with 640.  Hybrids: 17 = variant 12 for the first 6
-                                steps after a sort and variant 14 after them, 18 = the same
-                                switching after 4 steps.  0 = default (10).  All give identical
-                                results.  Other values: FETDPIC_EINVAL. */
+                                variant 9 with 640.  19 = variant 12 compiled for 14 blocks
+                                per SM (28 warps); 20 = variant 12 with a 256-triangle window.
+                                Hybrids: 17 = variant 12 for the first 6 steps after a sort and
+                                variant 14 after them, 18 = the same switching after 4 steps,
+                                21 = variant 19 for 6 steps then 14, 22 = variant 19 for 6
+                                steps then 20.  0 = default (22).  All give identical results.
+                                Other values: FETDPIC_EINVAL. */
     void *cuda_stream;       /* cudaStream_t to run on; NULL = a stream owned by the context */
     /* Optional device allocator (e.g. a framework's caching allocator).  NULL = cudaMalloc/cudaFree. */
     void *(*dev_alloc)(size_t bytes, void *user);

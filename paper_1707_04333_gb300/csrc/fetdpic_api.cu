@@ -184,6 +184,9 @@ struct fetdpic_ctx {
     }
 };
 
+// FP32 particle-kernel variant when the caller names none (see fetdpic_params.kernel_variant)
+constexpr int FP32_DEFAULT_VARIANT = 22;
+
 #define CK(call)                                                                     \
     do {                                                                             \
         cudaError_t _e = (call);                                                     \
@@ -247,10 +250,11 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
     if (P.block_size < 32 || P.block_size > 256 || (P.block_size & 31) || (SPECIES_ALIGN % P.block_size))
         return FETDPIC_EINVAL;
     if (P.record_walk < 0) return FETDPIC_EINVAL;
-    // untuned FP32 default: two particles per thread in 64-thread blocks (20 warps per SM at 96
-    // registers), measured fastest on the benchmark workload
-    if (P.kernel_variant < 0 || P.kernel_variant == 1 || P.kernel_variant > 18) return FETDPIC_EINVAL;
-    if (P.kernel_variant == 0) P.kernel_variant = 10;
+    // untuned FP32 default: the hybrid 22 (two particles per thread in 64-thread blocks, 28 warps
+    // per SM for 6 steps after a sort, then 24 warps per SM with a deposit window), measured fastest
+    // on the benchmark workload
+    if (P.kernel_variant < 0 || P.kernel_variant == 1 || P.kernel_variant > 22) return FETDPIC_EINVAL;
+    if (P.kernel_variant == 0) P.kernel_variant = FP32_DEFAULT_VARIANT;
     ctx->block = P.block_size;
     CK(cudaGetDevice(&ctx->device));
     if (P.cuda_stream) ctx->stream = (cudaStream_t)P.cuda_stream;
@@ -817,16 +821,29 @@ static StepArgs64 args64(fetdpic_ctx *ctx)
     return a;
 }
 
-// FP32 particle-kernel variant of the coming step.  The hybrids 17 and 18 run
-// variant 12 for the first 6 (17) or 4 (18) steps after a sort, while runs of
-// equal triangle are long, and the deposit-window variant 14 once the particles
-// have drifted; all variants give identical results.
+// Hybrid FP32 variants: (variant, early kernel variant, late kernel variant,
+// steps after a sort that run the early one).  While runs of equal triangle
+// are long (just after a sort) the early kernel runs; once the particles have
+// drifted, the late one with the deposit window.  All variants give identical
+// results.
+struct Hybrid { int v, early, late, steps; };
+static constexpr Hybrid HYBRIDS[] = {{17, 12, 14, 6}, {18, 12, 14, 4}, {21, 19, 14, 6}, {22, 19, 20, 6}};
+
+static const Hybrid *hybrid_of(int v)
+{
+    for (const Hybrid &h : HYBRIDS)
+        if (h.v == v) return &h;
+    return nullptr;
+}
+
+// FP32 particle-kernel variant of the coming step.
 static int step_variant(const fetdpic_ctx *ctx)
 {
     const int v = ctx->p.kernel_variant;
-    if (v != 17 && v != 18) return v;
+    const Hybrid *h = hybrid_of(v);
+    if (!h) return v;
     const long long since = ctx->p.sort_interval > 0 ? ctx->steps_done % ctx->p.sort_interval : ctx->steps_done;
-    return since < (v == 17 ? 6 : 4) ? 12 : 14;
+    return since < h->steps ? h->early : h->late;
 }
 
 static StepArgs32 args32(fetdpic_ctx *ctx)
@@ -991,8 +1008,8 @@ static int graph_step(fetdpic_ctx *ctx, int pusher, long long &launches)
     const bool sorts = ctx->p.sort_interval > 0 && ctx->nblocks > 0 &&
                        (ctx->steps_done + 1) % ctx->p.sort_interval == 0;
     const int parity = ctx->cell == ctx->cell_a ? 0 : 1;
-    const int kv = ctx->p.kernel_variant;
-    const int late = ctx->p.precision == FETDPIC_FP32 && (kv == 17 || kv == 18) && step_variant(ctx) == 14 ? 1 : 0;
+    const Hybrid *hy = hybrid_of(ctx->p.kernel_variant);
+    const int late = ctx->p.precision == FETDPIC_FP32 && hy && step_variant(ctx) == hy->late ? 1 : 0;
     cudaGraphExec_t &g = ctx->graph[pusher][parity][sorts ? 1 : 0][late];
     if (!g) {
         cudaGraph_t graph = nullptr;
@@ -1505,9 +1522,9 @@ extern "C" int fetdpic_set_wait_limit(fetdpic_ctx *ctx, long long wait_spin_limi
 extern "C" int fetdpic_set_tuning(fetdpic_ctx *ctx, int variant, int sort_interval)
 {
     if (!ctx) return FETDPIC_EINVAL;
-    if (variant < 0 || variant > 18 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
+    if (variant < 0 || variant > 22 || variant == 1 || sort_interval == 0) return ctx->fail(FETDPIC_EINVAL, "bad tuning");
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->p.kernel_variant = variant == 0 ? 10 : variant;    // 0 = the untuned default
+    ctx->p.kernel_variant = variant == 0 ? FP32_DEFAULT_VARIANT : variant;    // 0 = the untuned default
     ctx->p.sort_interval = sort_interval;
     drop_graphs(ctx);
     return FETDPIC_OK;
@@ -1556,7 +1573,8 @@ extern "C" int fetdpic_autotune(fetdpic_ctx *ctx, int pusher, int trial_steps, i
     ctx->p.check_interval = 0;
     ctx->probe_n = 0;
     rc = copy_state(true);
-    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 14, 17, 18} : std::vector<int>{3};
+    std::vector<int> variants = ctx->p.precision == FETDPIC_FP32 ? std::vector<int>{2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 14, 17, 18, 19, 20, 21, 22}
+                                                          : std::vector<int>{3};
     std::vector<int> sorts = keep_sort < 0 ? std::vector<int>{-1} : std::vector<int>{8, 12, 16, 32};
     double best = 1e300;
     int bv = keep_variant, bs = keep_sort;

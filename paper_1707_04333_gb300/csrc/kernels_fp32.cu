@@ -1025,6 +1025,8 @@ static void launch_p32v(cudaStream_t st, const StepArgs32 &a)
     case 10: launch_p32x2<PUSHER, 10, 2>(st, a); break;
     case 11: launch_p32x2<PUSHER, 6, 4, true>(st, a); break;
     case 12: launch_p32x2<PUSHER, 12, 2, true>(st, a); break;
+    case 19: launch_p32x2<PUSHER, 14, 2, true>(st, a); break;
+    case 20: launch_p32x2<PUSHER, 12, 2, true, 256>(st, a); break;
     case 13: launch_p32x2<PUSHER, 10, 2, false, 320>(st, a); break;
     case 14: launch_p32x2<PUSHER, 10, 2, false, 256>(st, a); break;
     case 15: launch_p32x2<PUSHER, 12, 2, true, 192>(st, a); break;

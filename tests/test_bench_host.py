@@ -23,8 +23,8 @@ def test_kernel_label_names_the_kernel_each_variant_launches():
     for v in (0, 8, 9, 10, 11, 12):
         assert b.kernel_label(v).startswith("k_particles32x2 ")
     assert "variant default" in b.kernel_label(0) and "variant 11" in b.kernel_label(11)
-    for v in (17, 18):
-        assert b.kernel_label(v).startswith("k_particles32x2 ") and "variant 14" in b.kernel_label(v)
+    for v in (17, 18, 21, 22):
+        assert b.kernel_label(v).startswith("k_particles32x2 ") and "then variant" in b.kernel_label(v)
 
 
 def test_traffic_reported_only_for_the_measured_sources(tmp_path):

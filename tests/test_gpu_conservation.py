@@ -44,7 +44,7 @@ def _oracle_from_gpu(oracle, w, pre, f0, fields=False):
     return ora
 
 
-@pytest.mark.parametrize("variant", [0, 9, 3, 5, 13, 16])
+@pytest.mark.parametrize("variant", [0, 9, 3, 5, 13, 16, 20])
 def test_fp32_sorted_pair_plasma_current_matches_oracle(fx, variant):
     """92,160 particles per species loaded in triangle order (sorted), sort every 4 steps, two steps
     past the sort (some particles have left their runs).  One step from the same state and fields:

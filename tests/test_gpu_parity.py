@@ -204,7 +204,7 @@ def test_deterministic_rerun(fx, precision):
             assert np.array_equal(a[k], b[k]), k
 
 
-@pytest.mark.parametrize("precision,variant", [("fp64", 0), ("fp32", 0), ("fp32", 18)])
+@pytest.mark.parametrize("precision,variant", [("fp64", 0), ("fp32", 0), ("fp32", 18), ("fp32", 10)])
 def test_graph_replay_equals_plain_launches(fx, precision, variant):
     """Steps replayed from captured CUDA graphs (all pushers' graphs, both particle-buffer parities,
     sorting and non-sorting steps, the sort on its side stream beside the Ampere update; for the
@@ -233,7 +233,7 @@ def test_fp32_kernel_variants_bit_identical(fx):
     fetdpic, _ = fx
     w = inputs.pair_plasma(48, 24, kT=0.3, seed=23, pusher="vay")
     outs = {}
-    for v in (3, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18):
+    for v in (3, 2, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22):
         s = fetdpic.Simulation(w, precision="fp32", spai_level=1, sort_interval=4, kernel_variant=v,
                                check_interval=5).load()
         s.step(5, "vay").step(4, "hc").step(6, "boris").sync()
@@ -241,7 +241,7 @@ def test_fp32_kernel_variants_bit_identical(fx):
         assert c["dce"] < 2e-5, (v, c)
         outs[v] = (s.read_fields(), s.read_species(0), s.read_species(1))
         s.close()
-    for v in (2, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18):
+    for v in (2, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18, 19, 20, 21, 22):
         for a, b in zip(outs[3], outs[v]):
             for k in a:
                 assert np.array_equal(a[k], b[k]), (v, k)
@@ -257,7 +257,7 @@ def test_autotune_leaves_state_unchanged(fx, precision, tmp_path):
     a.step(3, "vay")
     cache = str(tmp_path / "tune.json")
     v, s = a.autotune("vay", trial_steps=16, cache=cache)
-    assert v in range(2, 19) and s in (8, 12, 16, 32)
+    assert v in range(2, 23) and s in (8, 12, 16, 32)
     a.step(20, "vay").sync()
     b = fetdpic.Simulation(w, precision=precision, spai_level=1).load()
     b.step(3, "vay")
