@@ -239,6 +239,25 @@ int fetdpic_sync(fetdpic_ctx *ctx);
 int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
                  int species, double *x, double *u, int *cell);
 
+/* The particle part of fetdpic_read (x, u, cell of species `species`, load
+ * order, same values), without waiting: the state of the species as it is
+ * after the work already enqueued on the context stream is copied into a
+ * staging area of the species' own (kernel on the context stream), then to
+ * the host buffers on a stream of the context's own, while the context stream
+ * goes on with later writes, steps or reads.  So the host copy of one step's
+ * result can overlap the host-to-device copy of the next step's input.
+ *   - No counterpart in the paper: an interface for streaming the state.
+ *   - The host buffers (x [n][2], u [n][2], cell [n]; each may be NULL) must
+ *     stay valid and untouched until fetdpic_sync returns, which waits for
+ *     these copies too; from page-locked memory the copies run at the link's
+ *     rate.  Device status words are reported by that sync.
+ *   - A second asynchronous read of the same species waits, on the device,
+ *     until the first one's host copy has left the staging area.
+ *   - The first call allocates the staging areas (36 B per particle of every
+ *     species) and the stream.
+ * FETDPIC_EINVAL for a bad species; FETDPIC_ESTATE as fetdpic_read. */
+int fetdpic_read_particles_async(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell);
+
 /* Same particle output as fetdpic_read (x, u, cell of species `species`, load
  * order, FP32 positions converted), for callers that cannot allocate device
  * memory at the time of the call: real-time loops that forbid allocator

@@ -114,6 +114,14 @@ struct fetdpic_ctx {
     std::vector<std::vector<char>> abs_nodes; // per instance: nodes off the PEC walls (absolute reference 0)
     // reusable device scratch for host <-> device transfers of particle state
     void *xfer = nullptr; size_t xfer_bytes = 0;
+    // asynchronous particle reads: staging of their own (one region per species), copied to the
+    // host on the io stream while the context stream goes on; set up by the first such read
+    cudaStream_t io = nullptr;
+    cudaEvent_t ev_rd = nullptr;              // load-order copy done on the context stream
+    std::vector<cudaEvent_t> ev_rd_done;      // per species: its last host copy finished (io stream)
+    std::vector<char> rd_pending;             // per species: ev_rd_done has been recorded
+    char *rd_buf = nullptr;
+    std::vector<size_t> rd_off;
 
     // captured one-step graphs: [pusher][particle-buffer parity][step sorts][late hybrid step]
     cudaGraphExec_t graph[4][2][2][2] = {};
@@ -134,7 +142,10 @@ struct fetdpic_ctx {
     ~fetdpic_ctx()
     {
         cudaSetDevice(device);
+        // every stream of the context is idle before its memory goes back
         if (stream) cudaStreamSynchronize(stream);
+        if (side) cudaStreamSynchronize(side);
+        if (io) cudaStreamSynchronize(io);
         for (auto &a : graph) for (auto &b : a) for (auto &c : b) for (auto &g : c) if (g) cudaGraphExecDestroy(g);
         for (auto &a : cycle) for (auto &g : a) if (g) cudaGraphExecDestroy(g);
         for (void *q : allocs) {
@@ -142,7 +153,9 @@ struct fetdpic_ctx {
             else cudaFree(q);
         }
         for (auto &x : ev) cudaEventDestroy(x);
-        if (side) cudaStreamSynchronize(side);
+        for (auto &x : ev_rd_done) if (x) cudaEventDestroy(x);
+        if (ev_rd) cudaEventDestroy(ev_rd);
+        if (io) cudaStreamDestroy(io);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (side) cudaStreamDestroy(side);
@@ -1117,6 +1130,7 @@ extern "C" int fetdpic_sync(fetdpic_ctx *ctx)
 {
     if (!ctx) return FETDPIC_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->io) CK(cudaStreamSynchronize(ctx->io));      // host copies of asynchronous reads
     collect_events(ctx);
     return take_status(ctx);
 }
@@ -1126,6 +1140,8 @@ static void *xfer_buf(fetdpic_ctx *ctx, size_t bytes)
 {
     if (bytes <= ctx->xfer_bytes) return ctx->xfer;
     if (ctx->xfer) {
+        // an asynchronous write may still be copying into the old buffer
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return nullptr;
         for (size_t k = 0; k < ctx->allocs.size(); ++k)
             if (ctx->allocs[k] == ctx->xfer) { ctx->allocs.erase(ctx->allocs.begin() + k); break; }
         if (ctx->p.dev_free) ctx->p.dev_free(ctx->xfer, ctx->p.alloc_user);
@@ -1297,6 +1313,65 @@ extern "C" int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, do
         }
     }
     return take_status(ctx);
+}
+
+// Stream, events and staging of the asynchronous particle reads (first use).
+static int setup_async_reads(fetdpic_ctx *ctx)
+{
+    if (ctx->io) return FETDPIC_OK;
+    const size_t ns = ctx->sp.size();
+    size_t off = 0;
+    ctx->rd_off.assign(ns, 0);
+    for (size_t s = 0; s < ns; ++s) {
+        ctx->rd_off[s] = off;
+        off += ((36 * (size_t)ctx->sp[s].n + 255) / 256) * 256;      // x, u (FP64), cell per particle
+    }
+    try { ctx->rd_buf = ctx->alloc<char>(std::max<size_t>(off, 256)); } catch (const std::bad_alloc &) {
+        return FETDPIC_ENOMEM;
+    }
+    ctx->ev_rd_done.assign(ns, nullptr);
+    ctx->rd_pending.assign(ns, 0);
+    CK(cudaEventCreateWithFlags(&ctx->ev_rd, cudaEventDisableTiming));
+    for (auto &e : ctx->ev_rd_done) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    CK(cudaStreamCreateWithFlags(&ctx->io, cudaStreamNonBlocking));
+    return FETDPIC_OK;
+}
+
+extern "C" int fetdpic_read_particles_async(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell)
+{
+    if (!ctx) return FETDPIC_EINVAL;
+    int rc = finalize(ctx);
+    if (rc) return rc;
+    if (species < 0 || species >= (int)ctx->sp.size()) return ctx->fail(FETDPIC_EINVAL, "bad species");
+    CK(cudaSetDevice(ctx->device));
+    rc = setup_async_reads(ctx);
+    if (rc) return rc;
+    const Species &D = ctx->sp[species];
+    if (D.n == 0 || (!x && !u && !cell)) return FETDPIC_OK;
+    const size_t bx = sizeof(double) * 2 * D.n, bc = sizeof(int) * D.n;
+    char *st = ctx->rd_buf + ctx->rd_off[species];
+    double *ox = (double *)st, *ou = (double *)(st + bx);
+    int *oc = (int *)(st + 2 * bx);
+    // the previous asynchronous read of this species must have copied its staging out first
+    if (ctx->rd_pending[species]) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_rd_done[species], 0));
+    if (ctx->p.precision == FETDPIC_FP32)
+        launch_unsort32(ctx->stream, D.n, ctx->cell, ctx->id, (float *)ctx->f[0], (float *)ctx->f[1],
+                        (float *)ctx->f[2], (float *)ctx->f[3], ctx->geo64, ctx->p.c, D.off, D.cap, ctx->tri_i2c,
+                        ox, ou, oc);
+    else
+        launch_unsort64(ctx->stream, D.n, ctx->cell, ctx->id, (double *)ctx->f[0], (double *)ctx->f[1],
+                        (double *)ctx->f[2], (double *)ctx->f[3], D.off, D.cap, ctx->tri_i2c, ox, ou, oc);
+    CK(cudaGetLastError());
+    // the host copies run on the io stream: the context stream goes on with the next writes,
+    // steps or reads meanwhile (the state they change has already been copied to the staging)
+    CK(cudaEventRecord(ctx->ev_rd, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->io, ctx->ev_rd, 0));
+    if (x) CK(cudaMemcpyAsync(x, ox, bx, cudaMemcpyDeviceToHost, ctx->io));
+    if (u) CK(cudaMemcpyAsync(u, ou, bx, cudaMemcpyDeviceToHost, ctx->io));
+    if (cell) CK(cudaMemcpyAsync(cell, oc, bc, cudaMemcpyDeviceToHost, ctx->io));
+    CK(cudaEventRecord(ctx->ev_rd_done[species], ctx->io));
+    ctx->rd_pending[species] = 1;
+    return FETDPIC_OK;
 }
 
 extern "C" int fetdpic_read_charge(fetdpic_ctx *ctx, int inst, double *q, double *quantum)

@@ -77,6 +77,7 @@ def lib():
             "fetdpic_read_walk": (i32, [vp, i32, vp, vp]),
             "fetdpic_read_charge": (i32, [vp, i32, vp, vp]),
             "fetdpic_read_particles_static": (i32, [vp, i32, vp, vp, vp]),
+            "fetdpic_read_particles_async": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_check": (i32, [vp, i32, vp, vp, vp]),
             "fetdpic_info": (i32, [vp, i32, vp]),
             "fetdpic_read_edges": (i32, [vp, i32, vp]),
@@ -188,6 +189,16 @@ def fetdpic_read(h, inst=0, species=None, fields=True, n=None):
     if species is not None:
         out.update(x=x, u=u, cell=cell)
     return out
+
+
+def fetdpic_read_particles_async(h, species, x=None, u=None, cell=None):
+    """Enqueue the load-order read of one species into the given host arrays (x [n][2], u [n][2]
+    float64, cell [n] int32, C-contiguous; page-locked for full speed).  The arrays are filled when
+    fetdpic_sync returns and must be kept alive and untouched until then."""
+    for a, dt in ((x, np.float64), (u, np.float64), (cell, np.int32)):
+        if a is not None and (a.dtype != dt or not a.flags["C_CONTIGUOUS"]):
+            raise ValueError("fetdpic_read_particles_async: arrays must be C-contiguous float64 / int32")
+    _check(h, lib().fetdpic_read_particles_async(h, species, _ptr(x), _ptr(u), _ptr(cell)))
 
 
 def fetdpic_read_walk(h, species, n, cap):

@@ -347,3 +347,42 @@ def test_dropped_particle_changes_no_other_slot(fx, precision):
     scale = abs(s0.q) * n0 + abs(s1.q) * n1
     assert abs(q.sum() - expect) <= 1e-9 * scale + 3 * (n0 + n1) * quantum, (q.sum(), expect, s0.q)
     sim.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_async_particle_read_equals_read(fx, precision):
+    """fetdpic_read_particles_async returns exactly what fetdpic_read returns for the state left by
+    the work enqueued before it, also when later steps and writes change that state before the
+    host copies are awaited: three rounds of (steps with sorts, asynchronous read of both species,
+    species 0 overwritten from a stored state), all awaited by one fetdpic_sync, against a second
+    context that does the same with fetdpic_read."""
+    fetdpic, _ = fx
+    w = inputs.pair_plasma(16, 6, kT=0.2, wc_over_wp=0.5, seed=33, pusher="hc")
+    a = fetdpic.Simulation(w, precision=precision, spai_level=1, sort_interval=3).load()
+    b = fetdpic.Simulation(w, precision=precision, spai_level=1, sort_interval=3).load()
+    n = [len(s.x) for s in w.species]
+    ck = a.read_species(0)                   # stored state both contexts write back every round
+    got, ref = [], []
+    for r in range(3):
+        for sim in (a, b):
+            sim.step(2 + r, "hc")
+        bufs = []
+        for sid in range(2):
+            x = np.full((n[sid], 2), np.nan)
+            u = np.full((n[sid], 2), np.nan)
+            c = np.full(n[sid], -7, np.int32)
+            fetdpic.fetdpic_read_particles_async(a.h, sid, x, u, c)
+            bufs.append((x, u, c))
+        got.append(bufs)
+        ref.append([b.read_species(sid) for sid in range(2)])
+        for sim in (a, b):
+            fetdpic.fetdpic_write_particles(sim.h, 0, ck["x"], ck["u"], ck["cell"])
+    fetdpic.fetdpic_sync(a.h)
+    b.sync()
+    for r in range(3):
+        for sid in range(2):
+            x, u, c = got[r][sid]
+            g = ref[r][sid]
+            assert np.array_equal(x, g["x"]) and np.array_equal(u, g["u"]) and np.array_equal(c, g["cell"]), (r, sid)
+    a.close()
+    b.close()
