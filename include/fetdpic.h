@@ -255,7 +255,8 @@ int fetdpic_read(fetdpic_ctx *ctx, int inst, double *e, double *b, double *j,
  *     until the first one's host copy has left the staging area.
  *   - The first call allocates the staging areas (36 B per particle of every
  *     species) and the stream.
- * FETDPIC_EINVAL for a bad species; FETDPIC_ESTATE as fetdpic_read. */
+ * FETDPIC_EINVAL for a bad species; FETDPIC_ENOMEM if the staging cannot be
+ * allocated; FETDPIC_ECUDA for a failed launch or copy request. */
 int fetdpic_read_particles_async(fetdpic_ctx *ctx, int species, double *x, double *u, int *cell);
 
 /* Same particle output as fetdpic_read (x, u, cell of species `species`, load
