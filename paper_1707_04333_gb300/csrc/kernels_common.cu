@@ -32,10 +32,13 @@ __device__ __forceinline__ void spai_row(const AmpereArgs &a, const V *__restric
     a.e[a.m_row[row]] += (double)(s0 + s1);
 }
 
-// The same row with its static operands (slice offsets, output row, the first
-// two entries' values and columns) loaded before the wait for the kernel that
-// writes r, so their latency overlaps that kernel's end; same arithmetic and
-// order as spai_row.
+// The same row behind the wait for the kernel that writes r: before the wait
+// only the lines of its first two entries (values and columns, static) are
+// pulled into L1, so their latency overlaps that kernel's end while the row is
+// summed by spai_row itself (same loop, same order: the result is the same).
+// (Loading those entries into registers before the wait and entering the loop
+// after them gave the same on the 200k-triangle mesh but made the
+// bandwidth-bound SpMV of the 64-instance batch 13 % slower.)
 template <typename V>
 __device__ __forceinline__ void spai_row_pdl(const AmpereArgs &a, const V *__restrict__ v, const V *r,
                                              long long row, unsigned long long keep)
@@ -43,26 +46,17 @@ __device__ __forceinline__ void spai_row_pdl(const AmpereArgs &a, const V *__res
     const long long sl = row >> 5;
     const int lane = (int)(row & 31);
     const long long o0 = a.m_soff[sl], o1 = a.m_soff[sl + 1];
-    const int er = a.m_row[row];
-    long long q = o0 + lane;
-    V va = V(0), vb = V(0);
-    int ca = 0, cb = 0;
-    if (q < o1) { va = ld_keep(v + q, keep); ca = ld_keep(a.m_ci + q, keep); }
-    if (q + 32 < o1) { vb = ld_keep(v + q + 32, keep); cb = ld_keep(a.m_ci + q + 32, keep); }
-    pdl_begin();
-    V s0 = V(0), s1 = V(0);
-    if (q + 32 < o1) {
-        s0 += va * r[ca];
-        s1 += vb * r[cb];
-        for (q += 64; q + 32 < o1; q += 64) {
-            s0 += ld_keep(v + q, keep) * r[ld_keep(a.m_ci + q, keep)];
-            s1 += ld_keep(v + q + 32, keep) * r[ld_keep(a.m_ci + q + 32, keep)];
-        }
-        if (q < o1) s0 += ld_keep(v + q, keep) * r[ld_keep(a.m_ci + q, keep)];
-    } else if (q < o1) {
-        s0 += va * r[ca];
+    const long long q = o0 + lane;
+    if (q < o1) {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(v + q));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.m_ci + q));
     }
-    a.e[er] += (double)(s0 + s1);
+    if (q + 32 < o1) {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(v + q + 32));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(a.m_ci + q + 32));
+    }
+    pdl_begin();
+    spai_row<V>(a, v, r, row, keep);
 }
 
 // (Loading the face pairs and coefficients before the wait, as the SpMV does with
