@@ -62,6 +62,7 @@ struct fetdpic_ctx {
     double *inst_unit = nullptr, *inst_dt = nullptr;
     int *edge_off_dev = nullptr;
     long long *m_soff = nullptr; int *m_row = nullptr, *m_ci = nullptr; double *m_v = nullptr;
+    long long m_entries = 0;                  // stored SPAI entries (sliced ELL, padding included)
     float *m_v32 = nullptr, *r32 = nullptr;
     unsigned *status = nullptr;
     unsigned *gbar = nullptr;                // grid-barrier state of the fused Ampere launch (GBAR_WORDS)
@@ -574,6 +575,7 @@ extern "C" int fetdpic_create(fetdpic_ctx **out, const fetdpic_params *prm, int 
         rc = rc ? rc : upload(ctx, ctx->tri_i2c, i2c.data(), i2c.size());
     }
     rc = rc ? rc : upload(ctx, ctx->m_soff, soff.data(), soff.size());
+    ctx->m_entries = soff.back();
     rc = rc ? rc : upload(ctx, ctx->m_row, mrow.data(), mrow.size());
     rc = rc ? rc : upload(ctx, ctx->m_ci, sci.data(), sci.size());
     if (P.precision == FETDPIC_FP32) rc = rc ? rc : upload(ctx, ctx->m_v32, sv32.data(), sv32.size());
@@ -940,6 +942,7 @@ static long long enqueue_step(fetdpic_ctx *ctx, int pusher, bool timed)
     A.r = f32 ? nullptr : ctx->r; A.d = ctx->p.check_interval > 0 ? ctx->d : nullptr;
     A.j = ctx->j; A.r32 = ctx->r32;
     A.nfree = ctx->nfree; A.m_soff = ctx->m_soff; A.m_row = ctx->m_row; A.m_ci = ctx->m_ci; A.m_v = ctx->m_v;
+    A.m_entries = ctx->m_entries;
     A.m_v32 = ctx->m_v32;
     A.e = ctx->e;
     A.fused = ctx->p.fuse_field_update != 0;

@@ -246,6 +246,7 @@ struct AmpereArgs {
     long long nfree;
     // dt-scaled SPAI in sliced ELL: slice offsets, row -> edge, columns, values (FP64 or FP32)
     const long long *m_soff; const int *m_row; const int *m_ci; const double *m_v; const float *m_v32;
+    long long m_entries;                      // stored entries (padding included)
     double *e;
     // one cooperative launch for both phases (fused = true): its grid barrier's state (zero at
     // creation, left zero by every completed barrier, cleared by the host after a timeout), the

@@ -59,6 +59,10 @@ __device__ __forceinline__ void spai_row_pdl(const AmpereArgs &a, const V *__res
     spai_row<V>(a, v, r, row, keep);
 }
 
+// Matrices up to this size are prefetched before the wait (they stay in the
+// 129 MB L2 between steps, loaded with an evict-last policy).
+constexpr long long SPMV_PREFETCH_MAX_BYTES = 64ll << 20;
+
 // (Loading the face pairs and coefficients before the wait, as the SpMV does with
 // its operands, measured slower on GB300: 23.1 -> 26.5 us per step for the curl
 // and the SpMV together with stage events.)
@@ -70,13 +74,22 @@ __global__ void k_curl_h(AmpereArgs a)
     curl_h_edge(a, e, l2_keep());
 }
 
-template <typename V>
+// PRE: prefetch before the wait (a matrix that stays in L2: the SpMV is bound
+// by latency); else wait first (a large matrix: bound by HBM bandwidth, where
+// the prefetches only add requests).
+template <typename V, bool PRE>
 __global__ void __launch_bounds__(256) k_spai_sell(AmpereArgs a)
 {
     const long long row = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= a.nfree) { pdl_begin(); return; }
-    if constexpr (sizeof(V) == 4) spai_row_pdl<float>(a, a.m_v32, a.r32, row, l2_keep());
-    else spai_row_pdl<double>(a, a.m_v, a.r, row, l2_keep());
+    if (!PRE) pdl_begin();
+    if (row >= a.nfree) { if (PRE) pdl_begin(); return; }
+    if constexpr (PRE) {
+        if constexpr (sizeof(V) == 4) spai_row_pdl<float>(a, a.m_v32, a.r32, row, l2_keep());
+        else spai_row_pdl<double>(a, a.m_v, a.r, row, l2_keep());
+    } else {
+        if constexpr (sizeof(V) == 4) spai_row<float>(a, a.m_v32, a.r32, row, l2_keep());
+        else spai_row<double>(a, a.m_v, a.r, row, l2_keep());
+    }
 }
 
 
@@ -134,8 +147,16 @@ void launch_ampere(cudaStream_t st, const AmpereArgs &a)
     if (a.E > 0) launch_k(a.pdl, k_curl_h, dim3((a.E + 255) / 256), dim3(256), st, a);
     if (a.nfree > 0) {
         const dim3 g((unsigned)((a.nfree + 255) / 256));
-        if (a.m_v32) launch_k(a.pdl, k_spai_sell<float>, g, dim3(256), st, a);
-        else launch_k(a.pdl, k_spai_sell<double>, g, dim3(256), st, a);
+        // matrix bytes (values and columns, padding included) against what stays in L2
+        const long long bytes = a.m_entries * (long long)((a.m_v32 ? 4 : 8) + 4);
+        const bool pre = bytes <= SPMV_PREFETCH_MAX_BYTES;
+        if (a.m_v32) {
+            if (pre) launch_k(a.pdl, k_spai_sell<float, true>, g, dim3(256), st, a);
+            else launch_k(a.pdl, k_spai_sell<float, false>, g, dim3(256), st, a);
+        } else {
+            if (pre) launch_k(a.pdl, k_spai_sell<double, true>, g, dim3(256), st, a);
+            else launch_k(a.pdl, k_spai_sell<double, false>, g, dim3(256), st, a);
+        }
     }
 }
 
